@@ -1,0 +1,173 @@
+/*
+ * spectra_gb -- GB300 (sm_103a) boundary oracle and random walks for
+ * spectrahedra S = { x in R^n : F(x) = A_0 + sum_i x_i A_i >= 0 }
+ * (arXiv 2010.03817, "Efficient Sampling from Feasible Sets of SDPs and
+ * Volume Approximation", Eq. 1).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Return value: SP_OK (0) or one of the SP_E* codes below.  A non-zero
+ *   code means nothing was launched (argument errors) or a CUDA call failed
+ *   (SP_ECUDA); sp_last_error() gives a one-line message (thread-local).
+ * - "device" pointers are caller-owned global-memory pointers (for example
+ *   torch tensors' data_ptr()), contiguous, float64 unless stated.  The
+ *   library never frees or retains them past the call, and writes nothing
+ *   but the documented outputs.
+ * - "host" pointers are ordinary CPU memory.  Entry points that accept
+ *   "host or device" detect the kind with cudaPointerGetAttributes and copy
+ *   host data through their own staging buffers.
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *   enqueued asynchronously on it; outputs are ready when the stream is.
+ * - Per-item results carry a status word (SP_ST_*) in a caller buffer.
+ * - mode selects the arithmetic: SP_MODE_FP64 is the plain FP64 path.
+ *
+ * Handles own their device memory (allocated in the create/init calls,
+ * released by the matching destroy call).
+ */
+#ifndef SPECTRA_GB_H
+#define SPECTRA_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SP_OK 0
+#define SP_EINVAL 1      /* bad argument (null handle, size, mode, ...) */
+#define SP_ENOTPD 2      /* a start point is not interior: F(x) is not positive definite */
+#define SP_EUNBOUNDED 3  /* a ray never meets the boundary (S must be bounded) */
+#define SP_ENOCONV 4     /* an eigen-solve hit its iteration cap */
+#define SP_ECUDA 5       /* a CUDA runtime call failed */
+#define SP_ENOMEM 6      /* device allocation failed */
+
+/* per-item / per-chain status words */
+#define SP_ST_OK 0
+#define SP_ST_NOT_PD 1      /* point not interior (Cholesky of F failed) */
+#define SP_ST_UNBOUNDED 2   /* no positive root: t+ = +inf */
+#define SP_ST_NOCONV 3      /* Lanczos hit its cap; the result is the last Ritz value */
+#define SP_ST_RHO 4         /* Billiard: more than rho reflections, point kept (Alg. 5) */
+#define SP_ST_DEGENERATE 5  /* normal undefined: rank F(p+) <= m-2 (Lemma "Gradient of det F") */
+
+/* arithmetic modes */
+#define SP_MODE_FP64 0
+
+/* walk kinds (sp_chain_stats slots are SP_STAT_*) */
+#define SP_STAT_SEGMENTS 0     /* boundary-oracle calls */
+#define SP_STAT_REFLECTIONS 1  /* Billiard reflections */
+#define SP_STAT_BAD_STEPS 2    /* steps that ended with a non-OK status (point kept) */
+#define SP_STAT_LANCZOS 3      /* Lanczos iterations */
+#define SP_STAT_SHIFT_RETRY 4  /* shifted factorisations redone unshifted */
+#define SP_STAT_NOCONV 5       /* eigen-solves that hit the iteration cap */
+#define SP_NUM_STATS 8
+
+typedef struct sp_spec sp_spec;
+typedef struct sp_chains sp_chains;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sp_last_error(void);
+
+/* Library version string. */
+const char* sp_version(void);
+
+/*
+ * Create a spectrahedron handle from the LMI F(x) = A_0 + sum x_i A_i (Eq. 1).
+ *   n, m  : dimension and matrix size, 1 <= n <= 4096, 1 <= m <= 4096.
+ *   A     : host pointer, (n+1) x m x m float64 row-major, A[0] = A_0.  Each
+ *           A_i must be symmetric (checked to 1e-12 relative; SP_EINVAL
+ *           otherwise).  The library copies and packs it (lower triangles) to
+ *           device memory; the caller keeps ownership of A.
+ *   flags : reserved, pass 0.
+ *   out   : receives the handle; free with sp_destroy_spectrahedron.
+ */
+int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_spec** out);
+int sp_destroy_spectrahedron(sp_spec* s);
+int sp_spec_dims(const sp_spec* s, int* n, int* m);
+
+/*
+ * MEMBERSHIP (Sec. 2.2, Alg. 1) in the strict sense: inside[c] = 1 iff
+ * F(x_c) is positive definite (its Cholesky factorisation succeeds).
+ *   x: device, count x n.  inside: device int32, count.
+ */
+int sp_membership(sp_spec* s, int count, const double* x, int* inside, void* stream);
+
+/*
+ * INTERSECTION (Sec. 2.3, Alg. 2; Lemma "PEP and S cap C") for the lines
+ * x_c + t v_c: t_minus[c] < 0 < t_plus[c] are the roots of det(F(x_c) + t V_c)
+ * (V = sum v_i A_i) closest to 0 on either side.
+ *   x, v    : device, count x n (v need not be unit).
+ *   t_minus : device, count (-inf if none).   t_plus: device, count (+inf if none).
+ *   u       : device, count x m, or NULL: unit null vector of F(x + t+ v),
+ *             largest-magnitude entry positive.
+ *   status  : device int32, count (SP_ST_*).
+ *   mode    : SP_MODE_FP64.
+ */
+int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double* t_minus,
+                 double* t_plus, double* u, int* status, int mode, void* stream);
+
+/*
+ * REFLECTION (Sec. 2.4, Alg. 3; Eq. "reflection"; Lemma "Gradient of det F"):
+ * t_plus[c] as in sp_intersect, the unit normal w_hat = w/|w| with
+ * w_j = u^T A_j u (j = 1..n, u the null vector at the hit point; it points
+ * into S), and the reflected direction s = v - 2 <v, w_hat> w_hat.
+ *   x, v: device, count x n.  t_plus: device, count.  w_hat, s: device, count x n.
+ *   status: device int32, count.
+ */
+int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* t_plus,
+               double* w_hat, double* s_out, int* status, int mode, void* stream);
+
+/*
+ * Chains: C independent walkers with state (x, step counter) on the device.
+ *   x0    : host or device, C x n start points, or NULL for the origin.
+ *           Every start point must be interior (checked: SP_ENOTPD).
+ *   seed  : Philox4x32-10 key.  Chain c draws from counter (chain0 + c, step, stream, i).
+ *   chain0: offset of this handle's chains in the Philox counter space
+ *           (lets several handles / GPUs share one seed without overlap).
+ */
+int sp_init_chains(sp_spec* s, int C, const double* x0, uint64_t seed, uint32_t chain0,
+                   sp_chains** out, void* stream);
+int sp_destroy_chains(sp_chains* ch);
+
+/*
+ * Billiard walk (Sec. 3.2, Alg. 5): `steps` steps on every chain.
+ *   tau   : length scale, l = -tau ln eta (the paper takes tau ~ diam(S)).
+ *   rho   : reflection bound; a step with more than rho reflections keeps its
+ *           start point (status SP_ST_RHO, counted in SP_STAT_BAD_STEPS).
+ *   kappa : after a hit at t+ the walker moves to (1 - kappa) t+ (0 <= kappa < 1),
+ *           keeping F positive definite; the remaining length drops by t+.
+ */
+int sp_step_billiard(sp_chains* ch, int steps, double tau, int rho, double kappa, int mode,
+                     void* stream);
+
+/* Hit-and-Run (Sec. 3.1, Alg. 4), uniform point on the chord [t-, t+]. */
+int sp_step_hnr(sp_chains* ch, int steps, int mode, void* stream);
+
+/* Coordinate-direction Hit-and-Run (Sec. 3.1, CDHR): direction e_j, j uniform. */
+int sp_step_cdhr(sp_chains* ch, int steps, int mode, void* stream);
+
+/*
+ * Chain state.
+ *   sp_get_state: x_out (host or device, C x n) <- current points; *step_out <-
+ *                 the next step number.  Synchronises `stream` when x_out is host.
+ *   sp_set_state: replace the points (host or device, C x n; interior is not
+ *                 re-checked) and the step number (resume from a checkpoint).
+ *   sp_chain_status: status (device int32, C) of each chain's last failed step
+ *                 (SP_ST_OK if none), and stats (host int64, SP_NUM_STATS) summed
+ *                 over chains since init (synchronises `stream`).
+ */
+int sp_get_state(sp_chains* ch, double* x_out, uint32_t* step_out, void* stream);
+int sp_set_state(sp_chains* ch, const double* x, uint32_t step, void* stream);
+int sp_chain_status(sp_chains* ch, int* status, long long* stats, void* stream);
+
+/* Tuning knobs of the FP64 path (defaults in parentheses):
+ *   kmax (96): Lanczos iteration cap; tol (1e-13): relative residual target;
+ *   sigma_frac (0.1): after a reflection the next factorisation is taken at
+ *   x + sigma v with sigma = sigma_frac * (previous t+), falling back to
+ *   sigma = 0 when that point is outside S. */
+int sp_set_solver(sp_spec* s, int kmax, double tol, double sigma_frac);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPECTRA_GB_H */

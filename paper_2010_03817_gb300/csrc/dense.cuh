@@ -1,0 +1,172 @@
+// CTA-wide dense kernels on one chain's matrices: packed Cholesky, inverse of
+// the 32x32 diagonal blocks, blocked triangular solves, full GEMV.
+// All routines are called by every thread of a CTA of SPG_THREADS threads.
+//
+// Storage: lower triangle packed row-major, element (i, k) at i(i+1)/2 + k.
+// After factor_cholesky + invert_diag_blocks the diagonal 32x32 blocks hold
+// the inverses of the corresponding blocks of L; the off-diagonal blocks hold
+// L.  The triangular solves use exactly that layout.
+#pragma once
+#include "common.cuh"
+
+namespace spg {
+
+constexpr int kBlk = 32;
+
+// In-place Cholesky G = L L^T of the packed lower triangle G (m x m).
+// col: scratch of m elements.  Returns true on success (CTA-uniform); on
+// failure *fail_col = first column whose pivot was not positive.
+template <typename T>
+__device__ bool factor_cholesky(T* G, int m, T* col, int* flag) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      T d = G[tri(j, j)];
+      if (!(d > T(0))) {
+        *flag = j + 1;
+      } else {
+        T l = sqrt(d);
+        G[tri(j, j)] = l;
+        col[j] = T(1) / l;
+      }
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const T rl = col[j];
+    for (int i = j + 1 + tid; i < m; i += SPG_THREADS) {
+      T v = G[tri(i, j)] * rl;
+      G[tri(i, j)] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    // trailing update of rows i > j, columns j < k <= i, flattened so that
+    // every lane of every warp has an element
+    const int s = m - j - 1;
+    const int total = s * (s + 1) / 2;
+    if (tid < total) {
+      int i = j + 1, off = tid;  // element (i, j+1+off)
+      while (off >= i - j) {
+        off -= i - j;
+        ++i;
+      }
+      for (int q = tid; q < total; q += SPG_THREADS) {
+        const int k = j + 1 + off;
+        G[tri(i, k)] -= col[i] * col[k];
+        off += SPG_THREADS;
+        while (i < m && off >= i - j) {
+          off -= i - j;
+          ++i;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Replace each diagonal 32x32 block D of the packed factor by D^{-1} (lower
+// triangular), in place.  One warp per block; row r of the inverse is built
+// from the rows above it (D X = I, forward substitution by rows).
+template <typename T>
+__device__ void invert_diag_blocks(T* L, int m) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = (m + kBlk - 1) / kBlk;
+  for (int b = wid; b < nb; b += SPG_WARPS) {
+    const int r0 = b * kBlk;
+    const int bs = min(kBlk, m - r0);
+    for (int r = 0; r < bs; ++r) {
+      // X[r][c] = -(sum_{k=c}^{r-1} D[r][k] X[k][c]) / D[r][r], X[r][r] = 1/D[r][r]
+      T val = T(0);
+      const T drr = L[tri(r0 + r, r0 + r)];
+      if (lane < r) {
+        T acc = T(0);
+        for (int k = lane; k < r; ++k) acc += L[tri(r0 + r, r0 + k)] * L[tri(r0 + k, r0 + lane)];
+        val = -acc / drr;
+      } else if (lane == r) {
+        val = T(1) / drr;
+      }
+      __syncwarp();
+      if (lane <= r) L[tri(r0 + r, r0 + lane)] = val;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// x <- L^{-1} x (forward), using inverted diagonal blocks.  s: scratch >= 32.
+template <typename T>
+__device__ void solve_lower(const T* L, T* x, int m, T* s) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = (m + kBlk - 1) / kBlk;
+  for (int b = 0; b < nb; ++b) {
+    const int r0 = b * kBlk;
+    const int bs = min(kBlk, m - r0);
+    // s_r = x_r - sum_{k < r0} L[r][k] x_k
+    for (int rr = wid; rr < bs; rr += SPG_WARPS) {
+      const int r = r0 + rr;
+      const T* row = L + tri(r, 0);
+      T acc = T(0);
+      for (int k = lane; k < r0; k += 32) acc += row[k] * x[k];
+      acc = warp_sum(acc);
+      if (lane == 0) s[rr] = x[r] - acc;
+    }
+    __syncthreads();
+    if (wid == 0 && lane < bs) {
+      const T* row = L + tri(r0 + lane, r0);
+      T acc = T(0);
+      for (int c = 0; c <= lane; ++c) acc += row[c] * s[c];
+      x[r0 + lane] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// x <- L^{-T} x (backward), using inverted diagonal blocks.
+// s: scratch >= SPG_WARPS*32 + 32.
+template <typename T>
+__device__ void solve_upper(const T* L, T* x, int m, T* s) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = (m + kBlk - 1) / kBlk;
+  T* part = s + kBlk;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int r0 = b * kBlk;
+    const int bs = min(kBlk, m - r0);
+    const int i = r0 + lane;
+    // partial sums of sum_{r >= r0+bs} L[r][i] x_r, rows split over warps
+    T acc = T(0);
+    if (lane < bs)
+      for (int r = r0 + bs + wid; r < m; r += SPG_WARPS) acc += L[tri(r, i)] * x[r];
+    part[wid * kBlk + lane] = acc;
+    __syncthreads();
+    if (wid == 0 && lane < bs) {
+      T t = x[i];
+#pragma unroll
+      for (int w = 0; w < SPG_WARPS; ++w) t -= part[w * kBlk + lane];
+      s[lane] = t;
+    }
+    __syncthreads();
+    if (wid == 0 && lane < bs) {
+      // z_i = sum_{r >= i in block} Dinv[r][i] s_r
+      T z = T(0);
+      for (int rr = lane; rr < bs; ++rr) z += L[tri(r0 + rr, i)] * s[rr];
+      x[i] = z;
+    }
+    __syncthreads();
+  }
+}
+
+// y <- alpha * (A x), A full m x m row-major (global memory), one warp per row.
+template <typename T>
+__device__ void gemv_full(const T* __restrict__ A, const T* x, T* y, int m, T alpha) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = wid; r < m; r += SPG_WARPS) {
+    const T* row = A + (size_t)r * m;
+    T acc = T(0);
+    for (int k = lane; k < m; k += 32) acc += row[k] * x[k];
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = alpha * acc;
+  }
+  __syncthreads();
+}
+
+}  // namespace spg

@@ -1,0 +1,443 @@
+// Plain FP64 path: one CTA runs the whole boundary oracle for one chain at a
+// time (persistent over chains).  Per segment:
+//   form F(p) = A_0 + sum p_j A_j and V = sum v_j A_j      (Eq. 1; Lemma
+//       "PEP and S cap C": the pencil B_0 + t B_1 of a line)
+//   Cholesky of F + sigma V (shared memory)                (Alg. 1 as the
+//       interior certificate)
+//   Lanczos on M_sigma = -L^{-1} V L^{-T}: t = sigma + 1/mu (Alg. 2)
+//   w_j = u^T A_j u, u = L^{-T} y                          (Lemma "Gradient
+//       of det F")
+//   t+ refined as -(u^T F u)/(u^T V u) = -(w_0 + p.w)/(v.w)
+//   reflection s = v - 2 <v, w^> w^                        (Eq. "reflection")
+// and the walk drivers of Alg. 4 (Hit-and-Run), CDHR and Alg. 5 (Billiard).
+#include <math.h>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "kernels.h"
+#include "lanczos.cuh"
+
+namespace spg {
+
+namespace {
+
+struct Smem {
+  double* L;     // packed factor (shared or global)
+  double* p;     // n: current point
+  double* v;     // n: direction
+  double* x0;    // n: start of the step
+  double* w;     // n+1: quadratic forms u^T A_j u
+  double* wh;    // n: unit normal
+  double* q;     // m
+  double* r;     // m
+  double* z;     // m
+  double* ymax;  // m
+  double* ymin;  // m
+  double* u;     // m
+  double* col;   // m
+  double* scr;   // 288 + 32
+  LanczosScalars* sc;
+  double* bc;    // small broadcast area (16 doubles)
+  int* ib;       // small int broadcast area (16 ints)
+};
+
+__host__ __device__ inline size_t align8(size_t b) { return (b + 7) & ~size_t(7); }
+
+// carve the dynamic shared memory
+__device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
+  Smem s;
+  double* q = base;
+  const long long P = (long long)m * (m + 1) / 2;
+  if (l_in_smem) {
+    s.L = q;
+    q += P;
+  } else {
+    s.L = Lg;
+  }
+  s.p = q; q += n;
+  s.v = q; q += n;
+  s.x0 = q; q += n;
+  s.w = q; q += n + 1;
+  s.wh = q; q += n;
+  s.q = q; q += m;
+  s.r = q; q += m;
+  s.z = q; q += m;
+  s.ymax = q; q += m;
+  s.ymin = q; q += m;
+  s.u = q; q += m;
+  s.col = q; q += m;
+  s.scr = q; q += 320;
+  s.bc = q; q += 16;
+  s.sc = reinterpret_cast<LanczosScalars*>(q);
+  q += (sizeof(LanczosScalars) + 7) / 8;
+  s.ib = reinterpret_cast<int*>(q);
+  return s;
+}
+
+struct SegResult {
+  double t_plus, t_minus, t_raw;
+  int status;
+  int iters;
+  int retried;
+};
+
+// One boundary-oracle evaluation for the line p + t v (CTA-wide).
+__device__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
+                                  double* __restrict__ Vfull, double* __restrict__ Fg,
+                                  double* __restrict__ Q, double sigma, bool want_min,
+                                  bool want_w) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = sp.n, m = sp.m;
+  const long long P = sp.P;
+  SegResult res;
+  res.retried = 0;
+  // ---- form F(p), V (one pass over the A stack) --------------------------
+  for (long long e = tid; e < P; e += SPG_THREADS) {
+    const double* Ae = sp.A + e;
+    double f = Ae[0], g = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double a = Ae[(size_t)(j + 1) * P];
+      f += sm.p[j] * a;
+      g += sm.v[j] * a;
+    }
+    Fg[e] = f;
+    sm.L[e] = f + sigma * g;
+    const uint32_t ik = sp.pidx[e];
+    const int i = ik >> 16, k = ik & 0xffff;
+    Vfull[(size_t)i * m + k] = g;
+    Vfull[(size_t)k * m + i] = g;
+  }
+  __syncthreads();
+  // ---- Cholesky of F + sigma V; unshifted retry if the shift overshot ----
+  for (;;) {
+    if (tid == 0) sm.ib[0] = 0;
+    __syncthreads();
+    bool ok = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+    if (ok) break;
+    if (sigma != 0.0) {
+      sigma = 0.0;
+      res.retried = 1;
+      for (long long e = tid; e < P; e += SPG_THREADS) sm.L[e] = Fg[e];
+      __syncthreads();
+      continue;
+    }
+    res.status = kNotPD;
+    res.t_plus = res.t_minus = res.t_raw = 0.0;
+    res.iters = 0;
+    return res;
+  }
+  invert_diag_blocks(sm.L, m);
+  // ---- Lanczos ------------------------------------------------------------
+  for (int i = tid; i < m; i += SPG_THREADS) sm.q[i] = 1.0 + 0.5 * sin(0.7 * i + 0.1);
+  __syncthreads();
+  LanczosOut lo = lanczos_extreme<double>(sm.L, Vfull, Q, sm.q, sm.r, sm.z, sm.scr, sm.ymax,
+                                          sm.ymin, m, wk.kmax, want_min, wk.tol, sm.sc);
+  res.iters = lo.iters;
+  res.status = lo.converged ? kOk : kNoConv;
+  res.t_plus = lo.theta_max > 0.0 ? sigma + 1.0 / lo.theta_max : INFINITY;
+  res.t_minus = (want_min && lo.theta_min < 0.0) ? sigma + 1.0 / lo.theta_min : -INFINITY;
+  res.t_raw = res.t_plus;
+  if (!(lo.theta_max > 0.0)) {
+    if (res.status == kOk) res.status = kUnbounded;
+    return res;
+  }
+  // ---- null vector u = L^{-T} y and the forms w_j = u^T A_j u --------------
+  for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = sm.ymax[i];
+  __syncthreads();
+  solve_upper(sm.L, sm.u, m, sm.scr);
+  {  // unit length, largest-magnitude entry positive
+    double a = 0.0;
+    for (int i = tid; i < m; i += SPG_THREADS) a += sm.u[i] * sm.u[i];
+    const double nrm = sqrt(block_sum(a, sm.sc->red));
+    if (tid == 0) {
+      int big = 0;
+      for (int i = 1; i < m; ++i)
+        if (fabs(sm.u[i]) > fabs(sm.u[big])) big = i;
+      sm.bc[0] = (sm.u[big] < 0.0 ? -1.0 : 1.0) / nrm;
+    }
+    __syncthreads();
+    const double sc = sm.bc[0];
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] *= sc;
+    __syncthreads();
+  }
+  if (!want_w) return res;
+  // U_e = u_i u_k (x2 off the diagonal) overwrites the factor
+  double* U = sm.L;
+  for (long long e = tid; e < P; e += SPG_THREADS) {
+    const uint32_t ik = sp.pidx[e];
+    const int i = ik >> 16, k = ik & 0xffff;
+    U[e] = (i == k ? 1.0 : 2.0) * sm.u[i] * sm.u[k];
+  }
+  __syncthreads();
+  for (int j = wid; j <= n; j += SPG_WARPS) {
+    const double* Aj = sp.A + (size_t)j * P;
+    double acc = 0.0;
+    for (long long e = lane; e < P; e += 32) acc += Aj[e] * U[e];
+    acc = warp_sum(acc);
+    if (lane == 0) sm.w[j] = acc;
+  }
+  __syncthreads();
+  // refined t+ = -(w_0 + p.w)/(v.w)
+  {
+    double num = 0.0, den = 0.0;
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      num += sm.p[j] * sm.w[j + 1];
+      den += sm.v[j] * sm.w[j + 1];
+    }
+    num = block_sum(num, sm.sc->red);
+    den = block_sum(den, sm.sc->red);
+    num += sm.w[0];
+    const double tr = -num / den;
+    // keep the refinement only when it is a correction of the Ritz value
+    if (den < 0.0 && tr > 0.0 && fabs(tr - res.t_plus) <= 1e-4 * res.t_plus) res.t_plus = tr;
+  }
+  __syncthreads();
+  return res;
+}
+
+// unit normal w^ = w_{1..n}/|w| into dst; returns |w|
+__device__ double unit_normal(const Smem& sm, int n, double* dst) {
+  double a = 0.0;
+  for (int j = threadIdx.x; j < n; j += SPG_THREADS) a += sm.w[j + 1] * sm.w[j + 1];
+  const double nw = sqrt(block_sum(a, sm.sc->red));
+  if (nw > 0.0)
+    for (int j = threadIdx.x; j < n; j += SPG_THREADS) dst[j] = sm.w[j + 1] / nw;
+  __syncthreads();
+  return nw;
+}
+
+__global__ void __launch_bounds__(SPG_THREADS, 1)
+    walk_fp64_kernel(DevSpec sp, DevWork wk, WalkParams wp) {
+  extern __shared__ double smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n, m = sp.m;
+  const size_t cta = blockIdx.x;
+  double* Vfull = wk.Vfull + cta * (size_t)m * m;
+  double* Fg = wk.Fg + cta * (size_t)sp.P;
+  double* Q = wk.Q + cta * (size_t)wk.kmax * m;
+  double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
+  Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg);
+
+  for (int c = blockIdx.x; c < wp.C; c += gridDim.x) {
+    double* xc = wp.X + (size_t)c * n;
+    long long* st = wp.stats + (size_t)c * kNumStats;
+    long long segs = 0, refl = 0, bad = 0, iters = 0, retries = 0, noconv = 0;
+    int last_status = kOk;
+    const uint32_t chain = wp.chain0 + (uint32_t)c;
+    for (int j = tid; j < n; j += SPG_THREADS) sm.x0[j] = xc[j];
+    __syncthreads();
+    for (int k = 0; k < wp.steps; ++k) {
+      const uint32_t step = wp.step0 + (uint32_t)k;
+      for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] = sm.x0[j];
+      // ---- direction ----------------------------------------------------
+      if (wp.kind == 2) {
+        const double uc = rng_uniform(wp.seed, chain, step, kStreamCoord);
+        int jc = (int)(uc * n);
+        jc = jc < n ? jc : n - 1;
+        for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = (j == jc) ? 1.0 : 0.0;
+        __syncthreads();
+      } else {
+        for (int i = tid; 2 * i < n; i += SPG_THREADS) {
+          double g0, g1;
+          rng_gauss_pair(wp.seed, chain, step, (uint32_t)i, &g0, &g1);
+          sm.v[2 * i] = g0;
+          if (2 * i + 1 < n) sm.v[2 * i + 1] = g1;
+        }
+        __syncthreads();
+        double a = 0.0;
+        for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.v[j];
+        const double nv = sqrt(block_sum(a, sm.sc->red));
+        for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] /= nv;
+        __syncthreads();
+      }
+      const double eta = rng_uniform(wp.seed, chain, step, kStreamEta);
+      int status = kOk;
+      if (wp.kind == 0) {
+        // ---- Billiard (Alg. 5) -------------------------------------------
+        double ell = -wp.tau * log(eta);
+        int nrefl = 0;
+        double sigma = 0.0;
+        for (;;) {
+          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true);
+          ++segs;
+          iters += r.iters;
+          retries += r.retried;
+          if (r.status == kNoConv) {
+            ++noconv;
+            r.status = kOk;  // the Ritz value is still the best estimate
+          }
+          if (r.status != kOk) {
+            status = r.status;
+            break;
+          }
+          if (r.t_plus < ell) {
+            // hit the boundary: move to (1 - kappa) t+ and reflect
+            const double tp = r.t_plus;
+            double* wh = sm.wh;
+            const double nw = unit_normal(sm, n, wh);
+            if (!(nw > 0.0)) {
+              status = kDegenerate;
+              break;
+            }
+            double a = 0.0;
+            for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * wh[j];
+            const double vw = block_sum(a, sm.sc->red);
+            for (int j = tid; j < n; j += SPG_THREADS) {
+              sm.p[j] += (1.0 - wp.kappa) * tp * sm.v[j];
+              sm.v[j] -= 2.0 * vw * wh[j];
+            }
+            __syncthreads();
+            ell -= tp;
+            ++nrefl;
+            if (nrefl > wp.rho) {
+              status = kRho;
+              break;
+            }
+            sigma = wp.sigma_frac * tp;
+          } else {
+            for (int j = tid; j < n; j += SPG_THREADS) sm.x0[j] = sm.p[j] + ell * sm.v[j];
+            __syncthreads();
+            break;
+          }
+        }
+        refl += nrefl;
+      } else {
+        // ---- Hit-and-Run (Alg. 4) / CDHR: uniform point on the chord ------
+        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false);
+        ++segs;
+        iters += r.iters;
+        if (r.status == kNoConv) {
+          ++noconv;
+          r.status = kOk;
+        }
+        if (r.status == kOk && !(isfinite(r.t_plus) && isfinite(r.t_minus))) r.status = kUnbounded;
+        if (r.status == kOk) {
+          const double t = r.t_minus + eta * (r.t_plus - r.t_minus);
+          for (int j = tid; j < n; j += SPG_THREADS) sm.x0[j] = sm.p[j] + t * sm.v[j];
+          __syncthreads();
+        } else {
+          status = r.status;
+        }
+      }
+      if (status != kOk) {
+        ++bad;
+        last_status = status;
+      }
+      __syncthreads();
+    }
+    for (int j = tid; j < n; j += SPG_THREADS) xc[j] = sm.x0[j];
+    if (tid == 0) {
+      st[kStatSegments] += segs;
+      st[kStatReflections] += refl;
+      st[kStatBadSteps] += bad;
+      st[kStatLanczos] += iters;
+      st[kStatShiftRetry] += retries;
+      st[kStatNoConv] += noconv;
+      wp.status[c] = last_status;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SPG_THREADS, 1)
+    prim_fp64_kernel(DevSpec sp, DevWork wk, PrimParams pp) {
+  extern __shared__ double smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n, m = sp.m;
+  const size_t cta = blockIdx.x;
+  double* Vfull = wk.Vfull + cta * (size_t)m * m;
+  double* Fg = wk.Fg + cta * (size_t)sp.P;
+  double* Q = wk.Q + cta * (size_t)wk.kmax * m;
+  double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
+  Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg);
+  for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      sm.p[j] = pp.x[(size_t)c * n + j];
+      sm.v[j] = pp.op == 2 ? 0.0 : pp.v[(size_t)c * n + j];
+    }
+    __syncthreads();
+    if (pp.op == 2) {
+      // membership: Cholesky of F(x) succeeds
+      const long long P = sp.P;
+      for (long long e = tid; e < P; e += SPG_THREADS) {
+        const double* Ae = sp.A + e;
+        double f = Ae[0];
+        for (int j = 0; j < n; ++j) f += sm.p[j] * Ae[(size_t)(j + 1) * P];
+        sm.L[e] = f;
+      }
+      if (tid == 0) sm.ib[0] = 0;
+      __syncthreads();
+      bool ok = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+      if (tid == 0) pp.inside[c] = ok ? 1 : 0;
+      __syncthreads();
+      continue;
+    }
+    SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, pp.op == 0, true);
+    int status = r.status;
+    if (pp.op == 0) {
+      if (tid == 0) {
+        pp.t_plus[c] = r.t_plus;
+        pp.t_minus[c] = r.t_minus;
+        pp.status[c] = status;
+      }
+      if (pp.u && (status == kOk || status == kNoConv))
+        for (int i = tid; i < m; i += SPG_THREADS) pp.u[(size_t)c * m + i] = sm.u[i];
+    } else {
+      double* wh = sm.wh;
+      double nw = 0.0;
+      if (status == kOk || status == kNoConv) {
+        nw = unit_normal(sm, n, wh);
+        if (!(nw > 0.0)) status = kDegenerate;
+      }
+      if (status == kOk || status == kNoConv) {
+        double a = 0.0;
+        for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * wh[j];
+        const double vw = block_sum(a, sm.sc->red);
+        for (int j = tid; j < n; j += SPG_THREADS) {
+          pp.w_hat[(size_t)c * n + j] = wh[j];
+          pp.s[(size_t)c * n + j] = sm.v[j] - 2.0 * vw * wh[j];
+        }
+      }
+      if (tid == 0) {
+        pp.t_plus[c] = r.t_plus;
+        pp.status[c] = status;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t fp64_smem_bytes(int n, int m, bool l_in_smem) {
+  const size_t P = (size_t)m * (m + 1) / 2;
+  size_t d = (l_in_smem ? P : 0) + 4 * (size_t)n + (n + 1) + 7 * (size_t)m + 320 + 16;
+  size_t b = d * 8 + align8(sizeof(LanczosScalars)) + 16 * sizeof(int);
+  return b;
+}
+
+cudaError_t launch_walk_fp64(const DevSpec& sp, const DevWork& wk, const WalkParams& wp,
+                             cudaStream_t st) {
+  const size_t smem = fp64_smem_bytes(sp.n, sp.m, wk.l_in_smem);
+  cudaError_t e = cudaFuncSetAttribute(walk_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = wp.C < wk.ctas ? wp.C : wk.ctas;
+  if (grid <= 0) return cudaSuccess;
+  walk_fp64_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wk, wp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_fp64(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
+                             cudaStream_t st) {
+  const size_t smem = fp64_smem_bytes(sp.n, sp.m, wk.l_in_smem);
+  cudaError_t e = cudaFuncSetAttribute(prim_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = pp.count < wk.ctas ? pp.count : wk.ctas;
+  if (grid <= 0) return cudaSuccess;
+  prim_fp64_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wk, pp);
+  return cudaGetLastError();
+}
+
+}  // namespace spg

@@ -1,0 +1,257 @@
+"""Python binding of libspectra_gb (argument marshalling only).
+
+Every computation runs in the CUDA library behind the C ABI declared in
+``include/spectra_gb.h``; this module only converts torch tensors to device
+pointers and return codes to exceptions.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspectra_gb.so")
+
+OK, EINVAL, ENOTPD, EUNBOUNDED, ENOCONV, ECUDA, ENOMEM = range(7)
+ST_OK, ST_NOT_PD, ST_UNBOUNDED, ST_NOCONV, ST_RHO, ST_DEGENERATE = range(6)
+MODE_FP64 = 0
+MODES = {"fp64": MODE_FP64}
+STAT_NAMES = ["segments", "reflections", "bad_steps", "lanczos_iters", "shift_retries",
+              "noconv"]
+NUM_STATS = 8
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+class SpectraError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("spectra_gb error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _bind(L):
+    def f(name, args, res=ctypes.c_int):
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    f("sp_last_error", [], ctypes.c_char_p)
+    f("sp_version", [], ctypes.c_char_p)
+    f("sp_create_spectrahedron", [_i, _i, _vp, ctypes.c_uint32, ctypes.POINTER(_vp)])
+    f("sp_destroy_spectrahedron", [_vp])
+    f("sp_spec_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
+    f("sp_set_solver", [_vp, _i, _d, _d])
+    f("sp_membership", [_vp, _i, _vp, _vp, _vp])
+    f("sp_intersect", [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp])
+    f("sp_reflect", [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp])
+    f("sp_init_chains", [_vp, _i, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_vp),
+                         _vp])
+    f("sp_destroy_chains", [_vp])
+    f("sp_step_billiard", [_vp, _i, _d, _i, _d, _i, _vp])
+    f("sp_step_hnr", [_vp, _i, _i, _vp])
+    f("sp_step_cdhr", [_vp, _i, _i, _vp])
+    f("sp_get_state", [_vp, _vp, ctypes.POINTER(ctypes.c_uint32), _vp])
+    f("sp_set_state", [_vp, _vp, ctypes.c_uint32, _vp])
+    f("sp_chain_status", [_vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp])
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libspectra_gb.so is not built (run paper_2010_03817_gb300/"
+                                   "build.py or __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            _bind(L)
+            _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise SpectraError(code, lib().sp_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dev(t, dtype=None, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
+    return _vp(t.data_ptr())
+
+
+def version() -> str:
+    return lib().sp_version().decode()
+
+
+class Spectrahedron:
+    """Device-resident LMI F(x) = A_0 + sum_i x_i A_i (Eq. 1).
+
+    A: (n+1, m, m) float64 array-like on the host."""
+
+    def __init__(self, A):
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+        if A.ndim != 3 or A.shape[1] != A.shape[2]:
+            raise ValueError("A must be (n+1) x m x m")
+        self.n = A.shape[0] - 1
+        self.m = A.shape[1]
+        h = _vp()
+        _check(lib().sp_create_spectrahedron(self.n, self.m, A.ctypes.data_as(_vp), 0,
+                                             ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sp_destroy_spectrahedron(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_solver(self, kmax: int = 96, tol: float = 1e-13, sigma_frac: float = 0.1):
+        _check(lib().sp_set_solver(self._h, kmax, tol, sigma_frac))
+
+    # -- primitives ---------------------------------------------------------
+    def membership(self, x, stream=None):
+        import torch
+        C = x.shape[0]
+        inside = torch.empty(C, dtype=torch.int32, device=x.device)
+        _check(lib().sp_membership(self._h, C, _dev(x, torch.float64, (C, self.n), "x"),
+                                   _dev(inside), _stream(stream)))
+        return inside
+
+    def intersect(self, x, v, want_u: bool = False, mode: str = "fp64", stream=None):
+        """Alg. 2 for the lines x_c + t v_c: (t_minus, t_plus, u or None, status)."""
+        import torch
+        C = x.shape[0]
+        dev = x.device
+        tm = torch.empty(C, dtype=torch.float64, device=dev)
+        tp = torch.empty(C, dtype=torch.float64, device=dev)
+        st = torch.empty(C, dtype=torch.int32, device=dev)
+        u = torch.empty((C, self.m), dtype=torch.float64, device=dev) if want_u else None
+        _check(lib().sp_intersect(self._h, C, _dev(x, torch.float64, (C, self.n), "x"),
+                                  _dev(v, torch.float64, (C, self.n), "v"), _dev(tm), _dev(tp),
+                                  _dev(u) if want_u else None, _dev(st), MODES[mode],
+                                  _stream(stream)))
+        return tm, tp, u, st
+
+    def reflect(self, x, v, mode: str = "fp64", stream=None):
+        """Alg. 3 for the lines x_c + t v_c: (t_plus, w_hat, s, status)."""
+        import torch
+        C = x.shape[0]
+        dev = x.device
+        tp = torch.empty(C, dtype=torch.float64, device=dev)
+        wh = torch.empty((C, self.n), dtype=torch.float64, device=dev)
+        s = torch.empty((C, self.n), dtype=torch.float64, device=dev)
+        st = torch.empty(C, dtype=torch.int32, device=dev)
+        _check(lib().sp_reflect(self._h, C, _dev(x, torch.float64, (C, self.n), "x"),
+                                _dev(v, torch.float64, (C, self.n), "v"), _dev(tp), _dev(wh),
+                                _dev(s), _dev(st), MODES[mode], _stream(stream)))
+        return tp, wh, s, st
+
+
+class Chains:
+    """C independent walkers on a Spectrahedron (state on the device)."""
+
+    def __init__(self, spec: Spectrahedron, C: int, x0=None, seed: int = 0, chain0: int = 0,
+                 stream=None):
+        import torch
+        self.spec = spec
+        self.C = C
+        h = _vp()
+        if x0 is None:
+            ptr = None
+        elif isinstance(x0, torch.Tensor) and x0.is_cuda:
+            ptr = _dev(x0, torch.float64, (C, spec.n), "x0")
+        else:
+            x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+            if x0.shape != (C, spec.n):
+                raise ValueError("x0 must be (C, n)")
+            self._x0_host = x0
+            ptr = x0.ctypes.data_as(_vp)
+        _check(lib().sp_init_chains(spec.handle, C, ptr, seed, chain0, ctypes.byref(h),
+                                    _stream(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sp_destroy_chains(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def billiard(self, steps: int, tau: float, rho: int = 100, kappa: float = 1e-6,
+                 mode: str = "fp64", stream=None):
+        _check(lib().sp_step_billiard(self._h, steps, tau, rho, kappa, MODES[mode],
+                                      _stream(stream)))
+
+    def hnr(self, steps: int, mode: str = "fp64", stream=None):
+        _check(lib().sp_step_hnr(self._h, steps, MODES[mode], _stream(stream)))
+
+    def cdhr(self, steps: int, mode: str = "fp64", stream=None):
+        _check(lib().sp_step_cdhr(self._h, steps, MODES[mode], _stream(stream)))
+
+    def state(self, stream=None):
+        """(x as a CUDA float64 tensor (C, n), next step number)."""
+        import torch
+        x = torch.empty((self.C, self.spec.n), dtype=torch.float64, device="cuda")
+        step = ctypes.c_uint32(0)
+        _check(lib().sp_get_state(self._h, _dev(x), ctypes.byref(step), _stream(stream)))
+        return x, step.value
+
+    def state_host(self, out: np.ndarray | None = None, stream=None):
+        """Copy the points into a host array (synchronises the stream)."""
+        if out is None:
+            out = np.empty((self.C, self.spec.n), dtype=np.float64)
+        step = ctypes.c_uint32(0)
+        _check(lib().sp_get_state(self._h, out.ctypes.data_as(_vp), ctypes.byref(step),
+                                  _stream(stream)))
+        return out, step.value
+
+    def set_state(self, x, step: int, stream=None):
+        import torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            ptr = _dev(x, torch.float64, (self.C, self.spec.n), "x")
+        else:
+            x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+            ptr = x.ctypes.data_as(_vp)
+        _check(lib().sp_set_state(self._h, ptr, step, _stream(stream)))
+
+    def status(self, stream=None):
+        """(per-chain status tensor, dict of summed statistics)."""
+        import torch
+        st = torch.empty(self.C, dtype=torch.int32, device="cuda")
+        stats = (ctypes.c_longlong * NUM_STATS)()
+        _check(lib().sp_chain_status(self._h, _dev(st), stats, _stream(stream)))
+        return st, {k: int(stats[i]) for i, k in enumerate(STAT_NAMES)}
