@@ -30,6 +30,10 @@ N_DIM, M_DIM, CHAINS = 200, 200, 8192
 SEED_SPEC = 2010_03817 + 6   # S-200-200 workload seed
 SEED_WALK = 1234
 RHO, KAPPA = 1000, 1e-6
+# tau ~ diam(S) (Alg. 5).  For this workload: the longest chord through the
+# origin over 256 seeded random directions (a pilot run of the boundary
+# oracle), fixed here so that every arm uses the same value.
+TAU = 0.3752
 WORKLOAD = "Dabbene S-200-200 (n=m=200), 8192 chains, Billiard walk"
 
 
@@ -43,6 +47,9 @@ def parse():
     p.add_argument("--chains", type=int, default=CHAINS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--tau-scale", type=float, default=1.0,
+                   help="scale the length scale tau (a small value gives short steps, "
+                        "for profiling captures)")
     return p.parse_args()
 
 
@@ -149,7 +156,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     A = workload()
-    tau = 0.9  # fixed stand-in for the diameter estimate (the oracle arm needs no GPU)
+    tau = TAU
     times, segs = [], 0
     for i in range(args.warmup + args.steps):
         r = cpu_oracle_rate(A, tau, chains=16, steps=1)
@@ -178,12 +185,14 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def alg_flops_fp64(n, m, stats):
-    """Algorithmic FP64 flops of the plain path: per segment 2nP (V) + 2nP (F)
-    + m^3/3 (Cholesky) + 2(n+1)P (w); per Lanczos iteration 4m^2."""
+def alg_flops_fp64(n, m, stats, steps):
+    """Algorithmic FP64 flops of the plain path: per segment 2nP (V) +
+    m^3/3 (Cholesky) + 2(n+1)P (w); 2nP per step for F(x) at the step start,
+    2P per reflection for the carried F; 4m^2 per Lanczos iteration."""
     P = m * (m + 1) / 2
-    per_seg = 2 * n * P + 2 * n * P + m ** 3 / 3 + 2 * (n + 1) * P
-    return stats["segments"] * per_seg + stats["lanczos_iters"] * 4 * m * m
+    per_seg = 2 * n * P + m ** 3 / 3 + 2 * (n + 1) * P
+    return (stats["segments"] * per_seg + steps * 2 * n * P + stats["reflections"] * 2 * P
+            + stats["lanczos_iters"] * 4 * m * m)
 
 
 def main():
@@ -207,7 +216,7 @@ def main():
     lib = spectra.lib()
     A = workload()
     spec = spectra.Spectrahedron(A)
-    tau = estimate_tau(spec, torch)
+    tau = TAU * args.tau_scale
     C = args.chains
     X0 = start_points(A, C, rank)
     chains = spectra.Chains(spec, C, x0=X0, seed=SEED_WALK, chain0=rank * C)
@@ -247,7 +256,7 @@ def main():
     value = world * C * args.steps / (t_max / 1e3)
 
     # roofline of the dominant (and only) kernel: FP64 ALU bound
-    flops = alg_flops_fp64(N_DIM, M_DIM, seg_stats)
+    flops = alg_flops_fp64(N_DIM, M_DIM, seg_stats, C * args.steps)
     achieved = flops / (dev_ms / 1e3) / 1e12
     peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 

@@ -161,10 +161,90 @@ __device__ void gemv_full(const T* __restrict__ A, const T* x, T* y, int m, T al
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int r = wid; r < m; r += SPG_WARPS) {
     const T* row = A + (size_t)r * m;
-    T acc = T(0);
-    for (int k = lane; k < m; k += 32) acc += row[k] * x[k];
-    acc = warp_sum(acc);
+    T a0 = T(0), a1 = T(0);
+    int k = lane;
+    for (; k + 32 < m; k += 64) {
+      a0 += row[k] * x[k];
+      a1 += row[k + 32] * x[k + 32];
+    }
+    if (k < m) a0 += row[k] * x[k];
+    const T acc = warp_sum(a0 + a1);
     if (lane == 0) y[r] = alpha * acc;
+  }
+  __syncthreads();
+}
+
+// y <- alpha * (V z) for V symmetric, stored as a packed lower triangle
+// (shared or global memory).  One pass over the triangle: a warp reads row r
+// (coalesced) and uses V[r][k] twice, for y_r and for y_k (k < r), keeping the
+// second kind of contribution in per-lane registers (m <= 32 * kMaxColBlocks).
+// part: scratch of SPG_WARPS * m elements.
+constexpr int kMaxColBlocks = 16;
+template <typename T>
+__device__ void symv_packed(const T* __restrict__ V, const T* z, T* y, int m, T alpha, T* part) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T cacc[kMaxColBlocks];
+#pragma unroll
+  for (int i = 0; i < kMaxColBlocks; ++i) cacc[i] = T(0);
+  for (int r = wid; r < m; r += SPG_WARPS) {
+    const T* row = V + tri(r, 0);
+    const T zr = z[r];
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < kMaxColBlocks; ++i) {
+      const int k = lane + 32 * i;
+      if (k <= r) {
+        const T a = row[k];
+        acc += a * z[k];
+        if (k < r) cacc[i] += a * zr;
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = acc;  // row part; column parts added below
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxColBlocks; ++i) {
+    const int k = lane + 32 * i;
+    if (k < m) part[wid * m + k] = cacc[i];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += SPG_THREADS) {
+    T s = y[k];
+#pragma unroll
+    for (int w = 0; w < SPG_WARPS; ++w) s += part[w * m + k];
+    y[k] = alpha * s;
+  }
+  __syncthreads();
+}
+
+// y <- L^T x for the packed lower factor L (before invert_diag_blocks).
+// part: scratch of SPG_WARPS * m elements.
+template <typename T>
+__device__ void mul_upper(const T* L, const T* x, T* y, int m, T* part) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T cacc[kMaxColBlocks];
+#pragma unroll
+  for (int i = 0; i < kMaxColBlocks; ++i) cacc[i] = T(0);
+  for (int r = wid; r < m; r += SPG_WARPS) {
+    const T* row = L + tri(r, 0);
+    const T xr = x[r];
+#pragma unroll
+    for (int i = 0; i < kMaxColBlocks; ++i) {
+      const int k = lane + 32 * i;
+      if (k <= r) cacc[i] += row[k] * xr;  // (L^T x)_k = sum_{r >= k} L[r][k] x_r
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxColBlocks; ++i) {
+    const int k = lane + 32 * i;
+    if (k < m) part[wid * m + k] = cacc[i];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += SPG_THREADS) {
+    T s = T(0);
+#pragma unroll
+    for (int w = 0; w < SPG_WARPS; ++w) s += part[w * m + k];
+    y[k] = s;
   }
   __syncthreads();
 }

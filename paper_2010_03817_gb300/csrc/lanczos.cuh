@@ -102,6 +102,14 @@ __device__ R tri_eigvec(const double* a, const double* b, int K, R theta, R* s, 
       s[i] = (s[i] - (R)b[i] * s[i - 1]) / den;
     }
     for (int i = K - 2; i >= 0; --i) s[i] -= cw[i] * s[i + 1];
+    // scale by the largest entry first (the solve may produce huge values)
+    R mx = R(0);
+    for (int i = 0; i < K; ++i) mx = fmax(mx, fabs(s[i]));
+    if (!(mx > R(0)) || !isfinite(mx)) {
+      for (int i = 0; i < K; ++i) s[i] = (i == K - 1) ? R(1) : R(0);
+      mx = R(1);
+    }
+    for (int i = 0; i < K; ++i) s[i] /= mx;
     R nrm = R(0);
     for (int i = 0; i < K; ++i) nrm += s[i] * s[i];
     nrm = sqrt(nrm);
@@ -117,15 +125,28 @@ __device__ R tri_eigvec(const double* a, const double* b, int K, R theta, R* s, 
   return rq;
 }
 
-// r <- M_sigma q = -L^{-1} V L^{-T} q.  z: scratch vector (m), s: scratch (>=288)
+// The operator M_sigma = -L^{-1} V L^{-T}: L packed with inverted diagonal
+// blocks; V either full row-major (packed = false) or a packed lower
+// triangle (packed = true, `part` is the symv scratch of SPG_WARPS * m).
 template <typename T>
-__device__ void apply_pencil(const T* L, const T* __restrict__ Vfull, const T* q, T* r, T* z,
-                             int m, T* s) {
+struct PencilOp {
+  const T* L;
+  const T* V;
+  bool packed;
+  T* part;
+};
+
+// r <- M_sigma q.  z: scratch vector (m), s: scratch (>= 288)
+template <typename T>
+__device__ void apply_pencil(const PencilOp<T>& op, const T* q, T* r, T* z, int m, T* s) {
   for (int i = threadIdx.x; i < m; i += SPG_THREADS) z[i] = q[i];
   __syncthreads();
-  solve_upper(L, z, m, s);
-  gemv_full(Vfull, z, r, m, T(-1));
-  solve_lower(L, r, m, s);
+  solve_upper(op.L, z, m, s);
+  if (op.packed)
+    symv_packed(op.V, z, r, m, T(-1), op.part);
+  else
+    gemv_full(op.V, z, r, m, T(-1));
+  solve_lower(op.L, r, m, s);
 }
 
 struct LanczosOut {
@@ -140,9 +161,9 @@ struct LanczosOut {
 //   if want_min); r, z (m, smem) and s (>= 288, smem): scratch.
 //   tol: relative residual target |M y - theta y| <= tol |theta|.
 template <typename T>
-__device__ LanczosOut lanczos_extreme(const T* L, const T* __restrict__ Vfull, T* __restrict__ Q,
-                                      T* q, T* r, T* z, T* s, T* ymax, T* ymin, int m, int kmax,
-                                      bool want_min, double tol, LanczosScalars* sc) {
+__device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, T* q, T* r, T* z,
+                                      T* s, T* ymax, T* ymin, int m, int kmax, bool want_min,
+                                      double tol, LanczosScalars* sc) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   kmax = min(min(kmax, kMaxLanczos), m);
   // normalise q
@@ -161,7 +182,7 @@ __device__ LanczosOut lanczos_extreme(const T* L, const T* __restrict__ Vfull, T
   for (int k = 0; k < kmax; ++k) {
     T* Qk = Q + (size_t)k * m;
     for (int i = tid; i < m; i += SPG_THREADS) Qk[i] = q[i];
-    apply_pencil(L, Vfull, q, r, z, m, s);
+    apply_pencil(op, q, r, z, m, s);
     // two passes of classical Gram-Schmidt against Q[0..k]
     double alpha = 0.0;
     for (int pass = 0; pass < 2; ++pass) {

@@ -85,27 +85,57 @@ struct SegResult {
 __device__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
                                   double* __restrict__ Vfull, double* __restrict__ Fg,
                                   double* __restrict__ Q, double sigma, bool want_min,
-                                  bool want_w) {
+                                  bool want_w, bool form_f) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m;
   const long long P = sp.P;
   SegResult res;
   res.retried = 0;
-  // ---- form F(p), V (one pass over the A stack) --------------------------
-  for (long long e = tid; e < P; e += SPG_THREADS) {
-    const double* Ae = sp.A + e;
-    double f = Ae[0], g = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double a = Ae[(size_t)(j + 1) * P];
-      f += sm.p[j] * a;
-      g += sm.v[j] * a;
+  // ---- form V (and F(p) when form_f; otherwise F is carried in Fg) ---------
+  if (form_f) {
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const double* Ae = sp.A + e;
+      double f0 = Ae[0], f1 = 0.0, g0 = 0.0, g1 = 0.0;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        const double a0 = Ae[(size_t)(j + 1) * P], a1 = Ae[(size_t)(j + 2) * P];
+        f0 += sm.p[j] * a0;
+        g0 += sm.v[j] * a0;
+        f1 += sm.p[j + 1] * a1;
+        g1 += sm.v[j + 1] * a1;
+      }
+      if (j < n) {
+        const double a0 = Ae[(size_t)(j + 1) * P];
+        f0 += sm.p[j] * a0;
+        g0 += sm.v[j] * a0;
+      }
+      const double f = f0 + f1, g = g0 + g1;
+      Fg[e] = f;
+      sm.L[e] = f + sigma * g;
+      const uint32_t ik = sp.pidx[e];
+      const int i = ik >> 16, k = ik & 0xffff;
+      Vfull[(size_t)i * m + k] = g;
+      Vfull[(size_t)k * m + i] = g;
     }
-    Fg[e] = f;
-    sm.L[e] = f + sigma * g;
-    const uint32_t ik = sp.pidx[e];
-    const int i = ik >> 16, k = ik & 0xffff;
-    Vfull[(size_t)i * m + k] = g;
-    Vfull[(size_t)k * m + i] = g;
+  } else {
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const double* Ae = sp.A + e;
+      double g0 = 0.0, g1 = 0.0;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        g0 += sm.v[j] * Ae[(size_t)(j + 1) * P];
+        g1 += sm.v[j + 1] * Ae[(size_t)(j + 2) * P];
+      }
+      if (j < n) g0 += sm.v[j] * Ae[(size_t)(j + 1) * P];
+      const double g = g0 + g1;
+      sm.L[e] = Fg[e] + sigma * g;
+      const uint32_t ik = sp.pidx[e];
+      const int i = ik >> 16, k = ik & 0xffff;
+      Vfull[(size_t)i * m + k] = g;
+      Vfull[(size_t)k * m + i] = g;
+    }
   }
   __syncthreads();
   // ---- Cholesky of F + sigma V; unshifted retry if the shift overshot ----
@@ -130,8 +160,9 @@ __device__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm
   // ---- Lanczos ------------------------------------------------------------
   for (int i = tid; i < m; i += SPG_THREADS) sm.q[i] = 1.0 + 0.5 * sin(0.7 * i + 0.1);
   __syncthreads();
-  LanczosOut lo = lanczos_extreme<double>(sm.L, Vfull, Q, sm.q, sm.r, sm.z, sm.scr, sm.ymax,
-                                          sm.ymin, m, wk.kmax, want_min, wk.tol, sm.sc);
+  PencilOp<double> op{sm.L, Vfull, false, nullptr};
+  LanczosOut lo = lanczos_extreme<double>(op, Q, sm.q, sm.r, sm.z, sm.scr, sm.ymax, sm.ymin, m,
+                                          wk.kmax, want_min, wk.tol, sm.sc);
   res.iters = lo.iters;
   res.status = lo.converged ? kOk : kNoConv;
   res.t_plus = lo.theta_max > 0.0 ? sigma + 1.0 / lo.theta_max : INFINITY;
@@ -171,9 +202,16 @@ __device__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm
   __syncthreads();
   for (int j = wid; j <= n; j += SPG_WARPS) {
     const double* Aj = sp.A + (size_t)j * P;
-    double acc = 0.0;
-    for (long long e = lane; e < P; e += 32) acc += Aj[e] * U[e];
-    acc = warp_sum(acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long e = lane;
+    for (; e + 96 < P; e += 128) {
+      a0 += Aj[e] * U[e];
+      a1 += Aj[e + 32] * U[e + 32];
+      a2 += Aj[e + 64] * U[e + 64];
+      a3 += Aj[e + 96] * U[e + 96];
+    }
+    for (; e < P; e += 32) a0 += Aj[e] * U[e];
+    const double acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) sm.w[j] = acc;
   }
   __syncthreads();
@@ -258,7 +296,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
         int nrefl = 0;
         double sigma = 0.0;
         for (;;) {
-          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true);
+          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true, nrefl == 0);
           ++segs;
           iters += r.iters;
           retries += r.retried;
@@ -282,9 +320,14 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
             double a = 0.0;
             for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * wh[j];
             const double vw = block_sum(a, sm.sc->red);
+            const double step_len = (1.0 - wp.kappa) * tp;
             for (int j = tid; j < n; j += SPG_THREADS) {
-              sm.p[j] += (1.0 - wp.kappa) * tp * sm.v[j];
+              sm.p[j] += step_len * sm.v[j];
               sm.v[j] -= 2.0 * vw * wh[j];
+            }
+            for (long long e = tid; e < sp.P; e += SPG_THREADS) {
+              const uint32_t ik = sp.pidx[e];
+              Fg[e] += step_len * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
             }
             __syncthreads();
             ell -= tp;
@@ -303,7 +346,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
         refl += nrefl;
       } else {
         // ---- Hit-and-Run (Alg. 4) / CDHR: uniform point on the chord ------
-        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false);
+        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false, true);
         ++segs;
         iters += r.iters;
         if (r.status == kNoConv) {
@@ -372,7 +415,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       __syncthreads();
       continue;
     }
-    SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, pp.op == 0, true);
+    SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, pp.op == 0, true, true);
     int status = r.status;
     if (pp.op == 0) {
       if (tid == 0) {
