@@ -160,6 +160,36 @@ int sp_get_state(sp_chains* ch, double* x_out, uint32_t* step_out, void* stream)
 int sp_set_state(sp_chains* ch, const double* x, uint32_t step, void* stream);
 int sp_chain_status(sp_chains* ch, int* status, long long* stats, void* stream);
 
+/*
+ * INTERSECTION without any allocation (no counterpart in the paper; an
+ * interface for callers that cannot allocate device memory).
+ *
+ * Callers that live inside another runtime's memory pool, run under an
+ * allocator policy that forbids cudaMalloc, or sit in a loop where a driver
+ * allocation would stall, cannot create a spectrahedron handle (which owns
+ * device memory).  This entry point takes everything from the caller instead
+ * and allocates nothing: its working memory is one 8 MiB array of device
+ * memory declared statically in the library, present on every GPU that loads
+ * the library until the process exits.
+ *   n, m     : dimension and matrix size.  m is limited to what one thread
+ *              block's shared memory holds (about m <= 210), and the work
+ *              space of at least one block must fit in the 8 MiB array;
+ *              larger problems return SP_EINVAL.
+ *   A_packed : device, (n+1) x m(m+1)/2 float64, caller-owned: row j is the
+ *              lower triangle of A_j packed row by row (element (i, k), i >= k,
+ *              at i(i+1)/2 + k).
+ *   count, x, v, t_minus, t_plus, status: as in sp_intersect (device).
+ * Results equal those of sp_intersect (SP_MODE_FP64, default solver).  The
+ * first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array, which keeps whatever the previous call left in
+ * it: calls that overlap on the GPU (different streams or host threads) race
+ * and must be serialised by the caller.
+ */
+int sp_intersect_noalloc(int n, int m, const double* A_packed, int count, const double* x,
+                         const double* v, double* t_minus, double* t_plus, int* status,
+                         void* stream);
+
 /* Tuning knobs of the FP64 path (defaults in parentheses):
  *   kmax (96): Lanczos iteration cap; tol (1e-13): relative residual target;
  *   sigma_frac (0.1): after a reflection the next factorisation is taken at

@@ -149,6 +149,12 @@ extern "C" {
 
 const char* sp_last_error(void) { return g_err.c_str(); }
 
+// error reporting for entry points defined in other translation units
+int sp_noalloc_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 const char* sp_version(void) { return "spectra_gb 0.1 (sm_103a)"; }
 
 int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_spec** out) {

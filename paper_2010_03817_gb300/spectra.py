@@ -60,6 +60,7 @@ def _bind(L):
     f("sp_get_state", [_vp, _vp, ctypes.POINTER(ctypes.c_uint32), _vp])
     f("sp_set_state", [_vp, _vp, ctypes.c_uint32, _vp])
     f("sp_chain_status", [_vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp])
+    f("sp_intersect_noalloc", [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp])
 
 
 def lib():
@@ -98,6 +99,25 @@ def _dev(t, dtype=None, shape=None, name="tensor"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
     return _vp(t.data_ptr())
+
+
+def pack_lmi(A) -> np.ndarray:
+    """(n+1, m, m) stack -> (n+1, m(m+1)/2): lower triangles packed row by row."""
+    A = np.asarray(A, dtype=np.float64)
+    il = np.tril_indices(A.shape[1])
+    return np.ascontiguousarray(A[:, il[0], il[1]])
+
+
+def intersect_noalloc(A_packed, n: int, m: int, x, v, t_minus, t_plus, status, stream=None):
+    """sp_intersect_noalloc: every buffer is the caller's (CUDA tensors); the
+    library allocates nothing."""
+    import torch
+    C = x.shape[0]
+    _check(lib().sp_intersect_noalloc(
+        n, m, _dev(A_packed, torch.float64, (n + 1, m * (m + 1) // 2), "A_packed"), C,
+        _dev(x, torch.float64, (C, n), "x"), _dev(v, torch.float64, (C, n), "v"),
+        _dev(t_minus, torch.float64, (C,), "t_minus"), _dev(t_plus, torch.float64, (C,), "t_plus"),
+        _dev(status, torch.int32, (C,), "status"), _stream(stream)))
 
 
 def version() -> str:
