@@ -1,15 +1,22 @@
 """Benchmark: Billiard steps/s on the paper's random spectrahedron S-200-200
-(n = m = 200, Sec. 4 generator), 8192 independent chains, one GPU per rank.
+(n = m = 200, Sec. 4 generator), 8192 independent chains per GPU.
 
 A bench "step" is one Billiard step (Alg. 5) of every chain: each chain draws
-a direction and a length and runs the boundary oracle (form F, V; Cholesky;
-extreme eigenpair; normal; reflect) until the length is used up.  Chains are
-independent, so N GPUs run N replicas on disjoint chain ranges (weak scaling,
-no collective on the data path).
+a direction and a length and runs the boundary oracle (pencil, Cholesky,
+extreme eigenpair, normal, reflection) until the length is used up.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-(test infrastructure) on the host cores instead, on a bounded sample of the
-same workload.
+The headline path (--mode, default "learned") is timed for --steps steps after
+--warmup steps; the two other paths ("fp64": every step in FP64; "mixed":
+tensor-core formation, FP32 estimate, FP64 factorisation next to the boundary)
+are timed on the same workload for context (2 steps after 1 warm-up each).
+The learned path first trains its warm-start network on tuples recorded from
+a mixed-precision walk (outside the timed region).  Every path's t+ and
+normal are checked against the FP64 CPU oracle on sampled walk states.
+
+Chains are independent, so N GPUs run N replicas on disjoint chain ranges
+(weak scaling, no collective on the data path).  Prints one JSON line (rank
+0).  `--impl reference` times the FP64 CPU oracle (test infrastructure) on
+the host cores instead, on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -29,11 +36,13 @@ sys.path.insert(0, ROOT)
 N_DIM, M_DIM, CHAINS = 200, 200, 8192
 SEED_SPEC = 2010_03817 + 6   # S-200-200 workload seed
 SEED_WALK = 1234
+SEED_TRAIN = 4321
 RHO, KAPPA = 1000, 1e-6
 # tau ~ diam(S) (Alg. 5).  For this workload: the longest chord through the
 # origin over 256 seeded random directions (a pilot run of the boundary
 # oracle), fixed here so that every arm uses the same value.
 TAU = 0.3752
+T_SCALE = 0.05     # normalisation of log t+ for the warm-start network
 WORKLOAD = "Dabbene S-200-200 (n=m=200), 8192 chains, Billiard walk"
 
 
@@ -43,13 +52,18 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="fp64")
+    p.add_argument("--mode", default="learned", choices=["fp64", "mixed", "learned"])
+    p.add_argument("--only", action="store_true", help="time the --mode path alone")
     p.add_argument("--chains", type=int, default=CHAINS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-check", action="store_true", help="skip the sampled oracle check")
+    p.add_argument("--stage-timers", action="store_true",
+                   help="report the mixed path's per-stage cycle shares")
     p.add_argument("--tau-scale", type=float, default=1.0,
-                   help="scale the length scale tau (a small value gives short steps, "
-                        "for profiling captures)")
+                   help="scale tau (a small value gives short steps, for profiling captures)")
+    p.add_argument("--train-tuples", type=int, default=262144)
+    p.add_argument("--train-epochs", type=int, default=8)
     return p.parse_args()
 
 
@@ -58,19 +72,10 @@ def workload():
     return W.dabbene(N_DIM, M_DIM, seed=SEED_SPEC)
 
 
-def start_points(A, C, rank):
+def start_points(C, rank):
     # a small random cloud around the interior point x = 0
     from paper_2010_03817_gb300 import workloads as W
     return W.random_directions(N_DIM, C, seed=SEED_WALK + rank) * 1e-3
-
-
-def estimate_tau(spec, torch, C=256):
-    """tau ~ diameter (Alg. 5): the longest chord through 0 over random directions."""
-    from paper_2010_03817_gb300 import workloads as W
-    V = torch.tensor(W.random_directions(N_DIM, C, seed=99), device="cuda")
-    X = torch.zeros_like(V)
-    tm, tp, _, st = spec.intersect(X, V)
-    return float((tp - tm).max())
 
 
 # ----------------------------------------------------------------------------
@@ -136,7 +141,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 def cpu_oracle_rate(A, tau, chains=32, steps=1):
     import oracle
-    X0 = start_points(A, chains, 0)
+    X0 = start_points(chains, 0)
     t0 = time.perf_counter()
     _, stats = oracle.walk("billiard", A, X0, steps, tau=tau, rho=RHO, kappa=KAPPA,
                            seed=SEED_WALK)
@@ -156,10 +161,9 @@ def run_reference(args):
     import oracle
     oracle.build()
     A = workload()
-    tau = TAU
     times, segs = [], 0
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(A, tau, chains=16, steps=1)
+        r = cpu_oracle_rate(A, TAU, chains=16, steps=1)
         if i >= args.warmup:
             times.append(r["seconds"])
             segs += r["segments"]
@@ -183,16 +187,142 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
-# our arm
+# algorithmic work
 # ----------------------------------------------------------------------------
 def alg_flops_fp64(n, m, stats, steps):
-    """Algorithmic FP64 flops of the plain path: per segment 2nP (V) +
-    m^3/3 (Cholesky) + 2(n+1)P (w); 2nP per step for F(x) at the step start,
-    2P per reflection for the carried F; 4m^2 per Lanczos iteration."""
+    """FP64 flops of the plain path: per segment 2nP (V) + m^3/3 (Cholesky) +
+    2(n+1)P (normal); 2nP per step for F(x) at the step start, 2P per
+    reflection for the carried F; 4m^2 per Lanczos iteration."""
     P = m * (m + 1) / 2
     per_seg = 2 * n * P + m ** 3 / 3 + 2 * (n + 1) * P
     return (stats["segments"] * per_seg + steps * 2 * n * P + stats["reflections"] * 2 * P
             + stats["lanczos_iters"] * 4 * m * m)
+
+
+def alg_flops_wave_fp64(n, m, stats):
+    """FP64 flops of the mixed wave kernel: per segment the factorisation next
+    to the boundary (m^3/3), its fill (2P) and the carried-F update (2P); 4m^2
+    per FP64 power iteration."""
+    P = m * (m + 1) / 2
+    return stats["segments"] * (m ** 3 / 3 + 4 * P) + stats["power_iters"] * 4 * m * m
+
+
+def alg_flops_formation(n, m, segments):
+    """Tensor-core flops of the digit-split formation of V: 28 digit pairs of a
+    (rows x 16-padded K) x (K x P) product per segment."""
+    P = m * (m + 1) / 2
+    Kp = (n + 1 + 15) // 16 * 16
+    return segments * 28 * 2 * Kp * P
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# the walk on one path
+# ----------------------------------------------------------------------------
+def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, stage_timers=False):
+    chains = spectra.Chains(spec, C, x0=start_points(C, rank), seed=SEED_WALK, chain0=rank * C)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=mode)
+    torch.cuda.synchronize()
+    _, s0 = chains.status()
+    timers = None
+    if stage_timers and mode != "fp64":
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        timers = torch.zeros((sms, 8), dtype=torch.int64, device="cuda")
+        spec.set_stage_timers(timers)
+    chains.kernel_timing(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        evs[i][0].record(stream)
+        chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=mode)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    kt = chains.kernel_timing(0)
+    dev_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    _, s1 = chains.status()
+    stats = {k: s1[k] - s0[k] for k in s1}
+    share = None
+    if timers is not None:
+        spec.set_stage_timers(None)
+        tot = timers.sum(0).double()
+        names = ["fill+fp32_cholesky", "fp32_stage1_iterations", "fp64_fill+cholesky",
+                 "fp64_power", "fp64_fallback", "normal_contraction", "bookkeeping"]
+        share = {nm: float(tot[i] / tot.sum()) for i, nm in enumerate(names)}
+        share["cycles_per_segment"] = float(tot.sum()) / max(1, stats["segments"])
+    return dict(chains=chains, dev_ms=dev_ms, wall=wall, stats=stats, kt=kt, share=share,
+                steps=steps)
+
+
+def oracle_check(spectra, torch, spec, A, chains, mode, samples):
+    """t+ and normal of sampled walk states (x, v) against the FP64 oracle."""
+    import oracle
+    from paper_2010_03817_gb300 import workloads as W
+    x, _ = chains.state()
+    X = x[:samples].cpu().numpy()
+    V = W.random_directions(N_DIM, samples, seed=77)
+    tp, wh, s, st = spec.reflect(torch.tensor(X, device="cuda"), torch.tensor(V, device="cuda"),
+                                 mode=mode)
+    tp, wh, st = tp.cpu().numpy(), wh.cpu().numpy(), st.cpu().numpy()
+    et, ew = 0.0, 0.0
+    for c in range(samples):
+        r = oracle.reflect(A, X[c], V[c])
+        et = max(et, abs(tp[c] - r["t_plus"]) / abs(r["t_plus"]))
+        if r["rel_gap"] > 1e-6:
+            ew = max(ew, float(np.abs(wh[c] - r["w_hat"]).max()))
+    return {"t_rel_err_max": et, "normal_err_max": ew, "samples": samples,
+            "status_ok": bool((st == 0).all())}
+
+
+def train_network(spectra, torch, spec, C, epochs, tuples):
+    """Record (x, v) -> (log t+, u) tuples from a mixed-precision walk on the
+    same spectrahedron (other seed) and train the network on the GPU."""
+    t0 = time.perf_counter()
+    net = spectra.MLP(2 * N_DIM, 512, 1 + M_DIM, seed=SEED_TRAIN)
+    spec.attach_mlp(net, x_scale=1.0 / TAU, t_scale=T_SCALE, margin=0.05, iters=12)
+    X = torch.zeros((tuples, 2 * N_DIM), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((tuples, 1 + M_DIM), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ch = spectra.Chains(spec, C, x0=start_points(C, 99), seed=SEED_TRAIN)
+    ch.record(X, Y, cnt)
+    walk_steps = 0
+    while int(cnt.item()) < tuples and walk_steps < 64:
+        ch.billiard(1, tau=TAU, rho=RHO, kappa=KAPPA, mode="mixed")
+        walk_steps += 1
+    ch.record()
+    got = min(int(cnt.item()), tuples)
+    t1 = time.perf_counter()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    perm = torch.randperm(got, device="cuda", generator=g)
+    X, Y = X[perm].contiguous(), Y[perm].contiguous()
+    nval = max(8, got // 16 // 8 * 8)
+    ntr = (got - nval) // 1024 * 1024
+    losses = net.train(X[nval:nval + ntr].contiguous(), Y[nval:nval + ntr].contiguous(),
+                       epochs=epochs, batch=1024, lr=1e-3)
+    t2 = time.perf_counter()
+    Yp = net.forward(X[:nval].contiguous())
+    lt_err = (Yp[:, 0] - Y[:nval, 0]).abs()
+    cos = ((Yp[:, 1:] * Y[:nval, 1:]).sum(1).abs()
+           / (Yp[:, 1:].norm(dim=1) * Y[:nval, 1:].norm(dim=1)))
+    return net, {"tuples": got, "walk_steps": walk_steps, "record_s": t1 - t0,
+                 "train_s": t2 - t1, "epochs": epochs, "final_loss": float(losses[-1]),
+                 "val_rel_err_t_median": float(torch.expm1(lt_err).median()),
+                 "val_rel_err_t_p90": float(torch.expm1(lt_err).quantile(0.9)),
+                 "val_cos_u_median": float(cos.median())}
 
 
 def main():
@@ -213,56 +343,71 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    lib = spectra.lib()
+    spectra.lib()
     A = workload()
     spec = spectra.Spectrahedron(A)
     tau = TAU * args.tau_scale
     C = args.chains
-    X0 = start_points(A, C, rank)
-    chains = spectra.Chains(spec, C, x0=X0, seed=SEED_WALK, chain0=rank * C)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    train_info = None
+    if args.mode == "learned":
+        _net, train_info = train_network(spectra, torch, spec, min(C, 8192), args.train_epochs,
+                                         args.train_tuples)
 
-    for _ in range(args.warmup):
-        chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=args.mode)
-    torch.cuda.synchronize()
-    _, s0 = chains.status()
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    # context paths first (short), then the headline path under the clock sampler
+    context = {}
+    if not args.only:
+        for mode in ["fp64", "mixed", "learned"]:
+            if mode == args.mode or (mode == "learned" and train_info is None):
+                continue
+            context[mode] = time_path(spectra, torch, spec, mode, C, rank, 2, 1, tau, flush)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            evs[i][0].record(stream)
-            chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=args.mode)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+        head = time_path(spectra, torch, spec, args.mode, C, rank, args.steps, args.warmup, tau,
+                         flush, stage_timers=args.stage_timers)
     if world > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    dev_ms = float(sum(step_ms))
-    _, s1 = chains.status()
-    seg_stats = {k: s1[k] - s0[k] for k in s1}
-    t_max = dev_ms
+    t_max = head["dev_ms"]
     if world > 1:
-        t = torch.tensor([dev_ms], device="cuda")
+        t = torch.tensor([t_max], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
     value = world * C * args.steps / (t_max / 1e3)
+    st = head["stats"]
+    kt = head["kt"]
 
-    # roofline of the dominant (and only) kernel: FP64 ALU bound
-    flops = alg_flops_fp64(N_DIM, M_DIM, seg_stats, C * args.steps)
-    achieved = flops / (dev_ms / 1e3) / 1e12
+    # roofline of the dominant kernel of the headline path (FP64 pipe)
+    if args.mode == "fp64":
+        flops = alg_flops_fp64(N_DIM, M_DIM, st, C * args.steps)
+        ms = kt["fp64_ms"] or head["dev_ms"]
+        roof = {"bound": "alu", "kernel": "walk_fp64_kernel",
+                "launches": int(kt["fp64_launches"])}
+    else:
+        flops = alg_flops_wave_fp64(N_DIM, M_DIM, st)
+        ms = kt["wave_ms"] or head["dev_ms"]
+        roof = {"bound": "alu", "kernel": "mixed_wave_kernel",
+                "launches": int(kt["wave_launches"])}
     peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    achieved = flops / (ms / 1e3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
+                 "frac": achieved / peak, "traffic": None,
+                 "kernel_ms_per_step": ms / args.steps,
+                 "share_of_step": ms / max(1e-9, head["dev_ms"])})
+    formation = None
+    if args.mode != "fp64" and kt["form_ms"] > 0:
+        ff = alg_flops_formation(N_DIM, M_DIM, st["segments"])
+        fa = ff / (kt["form_ms"] / 1e3) / 1e12
+        peaks = _peaks()
+        formation = {"bound": "tensor", "kernel": "ozaki_form_kernel (+ digit slicing)",
+                     "achieved": fa, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": fa / peaks["bf16_tflops"], "peak_source": peaks["source"],
+                     "share_of_step": kt["form_ms"] / max(1e-9, head["dev_ms"])}
 
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        chains = head["chains"]
         xh, step = chains.state_host()
         xh = np.ascontiguousarray(xh)
         out = np.empty_like(xh)
@@ -277,7 +422,18 @@ def main():
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e = {"value": C * k / e2e_s * world, "unit": "steps/s",
-               "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+               "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes),
+               "note": "set_state from host, one Billiard step, get_state to host"}
+
+    checks = {}
+    if rank == 0 and not args.no_check:
+        try:
+            import oracle
+            oracle.build()
+            for mode, r in list(context.items()) + [(args.mode, head)]:
+                checks[mode] = oracle_check(spectra, torch, spec, A, r["chains"], mode, 3)
+        except Exception as exc:
+            checks = {"failed": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -288,30 +444,50 @@ def main():
             cpu = {"value": None, "unit": "steps/s", "cores": None, "kind": "oracle",
                    "sample": "failed: %s" % exc}
 
+    def summary(r):
+        s = r["stats"]
+        segs = max(1, s["segments"])
+        return {"steps_per_s": C * r["steps"] / (r["dev_ms"] / 1e3),
+                "ms_per_step": r["dev_ms"] / r["steps"],
+                "segments_per_step": s["segments"] / (C * r["steps"]),
+                "iters_per_segment": s["lanczos_iters"] / segs,
+                "fp64_power_iters_per_segment": s["power_iters"] / segs,
+                "fp64_fallback_rate": s["fp64_fallbacks"] / segs,
+                "warm_start_accept_rate": s["learned_ok"] / segs,
+                "bad_steps": s["bad_steps"], "steps": r["steps"]}
+
     if rank == 0:
+        paths = {m: summary(r) for m, r in context.items()}
+        paths[args.mode] = summary(head)
+        speedup = None
+        if "fp64" in paths and args.mode != "fp64":
+            speedup = paths[args.mode]["steps_per_s"] / paths["fp64"]["steps_per_s"]
+        launches = int(kt["fp64_launches"] + kt["form_launches"] + kt["wave_launches"]
+                       + kt["mlp_launches"] + kt["other_launches"])
         line = {
             "metric": "billiard steps/s at n=m=200",
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.mode == "fp64" else "f64+f32+bf16",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_DIM, "m": M_DIM, "chains_per_gpu": C,
                        "path": args.mode, "tau": tau, "rho": RHO, "kappa": KAPPA,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas x%d" % world},
-            "segments_per_step": seg_stats["segments"] / (C * args.steps),
-            "oracle_calls_per_s": seg_stats["segments"] * world / (t_max / 1e3),
-            "lanczos_iters_per_segment": seg_stats["lanczos_iters"] / max(1, seg_stats["segments"]),
-            "shift_retry_rate": seg_stats["shift_retries"] / max(1, seg_stats["segments"]),
-            "bad_steps": seg_stats["bad_steps"],
-            "roofline": {"bound": "alu", "kernel": "walk_fp64_kernel", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s (FP64)", "frac": achieved / peak,
-                         "traffic": None},
+            "oracle_calls_per_s": st["segments"] * world / (t_max / 1e3),
+            "paths": paths,
+            "speedup_vs_fp64": speedup,
+            "oracle_check": checks,
+            "training": train_info,
+            "stage_share": head["share"],
+            "roofline": roof,
+            "roofline_formation": formation,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
-            "wall_s_timed": wall,
+            "wall_s_timed": head["wall"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

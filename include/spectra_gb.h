@@ -19,7 +19,8 @@
  * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *   enqueued asynchronously on it; outputs are ready when the stream is.
  * - Per-item results carry a status word (SP_ST_*) in a caller buffer.
- * - mode selects the arithmetic: SP_MODE_FP64 is the plain FP64 path.
+ * - mode selects the arithmetic: SP_MODE_FP64 (plain FP64 path) or
+ *   SP_MODE_MIXED (see below).
  *
  * Handles own their device memory (allocated in the create/init calls,
  * released by the matching destroy call).
@@ -51,7 +52,12 @@ extern "C" {
 #define SP_ST_DEGENERATE 5  /* normal undefined: rank F(p+) <= m-2 (Lemma "Gradient of det F") */
 
 /* arithmetic modes */
-#define SP_MODE_FP64 0
+#define SP_MODE_FP64 0   /* every step in FP64 */
+#define SP_MODE_MIXED 1  /* tensor-core V formation (exact digit splitting, FP64 quality),
+                            FP32 estimate, FP64 factorisation next to the boundary and FP64
+                            refinement of t+ and u; needs n + 1 <= 224 */
+#define SP_MODE_LEARNED 2  /* the mixed path with the network's warm start (sp_attach_mlp)
+                              for the Billiard walk; primitives run as SP_MODE_MIXED */
 
 /* walk kinds (sp_chain_stats slots are SP_STAT_*) */
 #define SP_STAT_SEGMENTS 0     /* boundary-oracle calls */
@@ -60,7 +66,11 @@ extern "C" {
 #define SP_STAT_LANCZOS 3      /* Lanczos iterations */
 #define SP_STAT_SHIFT_RETRY 4  /* shifted factorisations redone unshifted */
 #define SP_STAT_NOCONV 5       /* eigen-solves that hit the iteration cap */
-#define SP_NUM_STATS 8
+#define SP_STAT_FALLBACK 6     /* mixed path: segments that fell back to an FP64 Lanczos */
+#define SP_STAT_POWER 7        /* mixed path: FP64 power iterations next to the boundary */
+#define SP_STAT_LEARNED_OK 8   /* learned path: warm starts accepted by the certificate */
+#define SP_STAT_LEARNED_MISS 9 /* learned path: warm starts rejected (plain stage 1 instead) */
+#define SP_NUM_STATS 12
 
 typedef struct sp_spec sp_spec;
 typedef struct sp_chains sp_chains;
@@ -116,6 +126,17 @@ int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double
  */
 int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* t_plus,
                double* w_hat, double* s_out, int* status, int mode, void* stream);
+
+/*
+ * The pencil of the lines x_c + t v_c (Lemma "PEP and S cap C"):
+ * F_out[c] = F(x_c) = A_0 + sum_i x_ci A_i and V_out[c] = sum_i v_ci A_i, as
+ * packed lower triangles (count x m(m+1)/2, device).  x / F_out or v / V_out
+ * may both be NULL.  SP_MODE_FP64: FP64 arithmetic.  SP_MODE_MIXED: BF16
+ * tensor cores with exact digit splitting of both operands (49-bit digits,
+ * FP64 result; error below (n+1) 2^-44 max_j |c_j| max_j |A_j[p]|).
+ */
+int sp_form_pencil(sp_spec* s, int count, const double* x, const double* v, double* F_out,
+                   double* V_out, int mode, void* stream);
 
 /*
  * Chains: C independent walkers with state (x, step counter) on the device.
@@ -189,6 +210,82 @@ int sp_chain_status(sp_chains* ch, int* status, long long* stats, void* stream);
 int sp_intersect_noalloc(int n, int m, const double* A_packed, int count, const double* x,
                          const double* v, double* t_minus, double* t_plus, int* status,
                          void* stream);
+
+/*
+ * The learned warm start (not in the paper): a three-layer perceptron
+ * din -> dh -> dh -> dout (ReLU) that maps a line (x, v) to (log t+, u) so
+ * that the boundary oracle can shift the pencil next to the boundary and
+ * start its eigen-iteration from u.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores; FP32 master weights, Adam.
+ * Parameter layout (floats): W1 [dh x ceil8(din)] (columns >= din zero),
+ * b1 [dh], W2 [dh x dh], b2 [dh], W3 [ceil16(dout) x dh] (rows >= dout
+ * zero), b3 [ceil16(dout)].
+ * Training loss per sample, batch mean:
+ *   (Y_0 - T_0)^2 + 1 - (a.b)^2 / (|a|^2 |b|^2),  a = Y_1.., b = T_1..
+ *   sp_mlp_create : dh a multiple of 8; He initialisation from `seed`.
+ *   sp_mlp_params : copy the parameters to host_out and / or from host_in (host).
+ *   sp_mlp_forward: X (device f32, count x din) -> Y (device f32, count x dout).
+ *   sp_mlp_gradients: one forward + backward on (X, T) (device, T count x dout,
+ *                   count a multiple of 8); gradients (host, parameter layout)
+ *                   and the loss (host).  Synchronises `stream`.
+ *   sp_mlp_train  : `epochs` passes of Adam over count / batch mini-batches in
+ *                   order; losses_host[e] = last mini-batch loss of epoch e.
+ */
+typedef struct sp_mlp sp_mlp;
+int sp_mlp_create(int din, int dh, int dout, uint64_t seed, sp_mlp** out);
+int sp_mlp_destroy(sp_mlp* q);
+int sp_mlp_dims(const sp_mlp* q, int* din, int* dh, int* dout, long long* nparams);
+int sp_mlp_params(sp_mlp* q, float* host_out, const float* host_in);
+int sp_mlp_forward(sp_mlp* q, int count, const float* X, float* Y, void* stream);
+int sp_mlp_gradients(sp_mlp* q, int count, const float* X, const float* T, float* grads_host,
+                     float* loss_host, void* stream);
+int sp_mlp_train(sp_mlp* q, int count, const float* X, const float* T, int epochs, int batch,
+                 float lr, float* losses_host, void* stream);
+
+/*
+ * Attach a warm-start network (din = 2n inputs (x * x_scale, v), dout = 1 + m
+ * outputs (log(t+ / t_scale), u)) to a spectrahedron for SP_MODE_LEARNED
+ * walks, or detach it (q = NULL).  The Billiard walk then factors
+ * F + sigma0 V at sigma0 = (1 - margin) t^ and runs at most `iters` FP32
+ * power iterations from the predicted u; a prediction that fails the
+ * certificate (convergence, positive dominant eigenvalue, t+ - sigma0 <
+ * sigma0) falls back to the plain stage 1.  The caller keeps ownership of q.
+ */
+int sp_attach_mlp(sp_spec* s, sp_mlp* q, double x_scale, double t_scale, double margin,
+                  int iters);
+
+/*
+ * Record training tuples during SP_MODE_MIXED / SP_MODE_LEARNED Billiard
+ * walks: each segment whose refinement succeeded appends
+ *   x_out[k] = (x * x_scale, v)          (2n floats),
+ *   y_out[k] = (log(t+ / t_scale), u)    (1 + m floats)
+ * with k = atomicAdd(*count, 1) while k < capacity (device buffers; the
+ * caller zeroes *count).  x_scale and t_scale are those of sp_attach_mlp
+ * (defaults 1).  Pass x_out = NULL to stop recording.
+ */
+int sp_record_tuples(sp_chains* ch, float* x_out, float* y_out, int capacity, int* count);
+
+/*
+ * Per-kernel timing of later walk calls on `ch` (CUDA events recorded on the
+ * walk's stream around each launch; the mixed path reads them between its
+ * waves, the FP64 path at the end of the call).  out (host, 9 doubles, may
+ * be NULL): [0] FP64 walk kernel ms, [1] its launches, [2] tensor-core
+ * formation ms, [3] its launches (digit slicing + GEMM), [4] mixed wave
+ * kernel ms, [5] its launches, [6] warm-start network ms, [7] its launches,
+ * [8] other launches.  enable: 1 on (counters reset), 0 off (reset), -1 read
+ * only.
+ */
+int sp_kernel_timing(sp_chains* ch, int enable, double* out);
+
+/*
+ * Stage timers of the mixed path (profiling aid).  timers: device int64
+ * array of (number of SMs) x 8 entries, zeroed by the caller, or NULL to
+ * switch the timers off.  Block b adds the clock64() cycles it spends in
+ * each stage of each segment to timers[8 b + k]: k = 0 stage-1 fill and FP32
+ * Cholesky, 1 FP32 Lanczos, 2 FP64 fill and Cholesky, 3 FP64 power
+ * iterations, 4 FP64 Lanczos fallback, 5 normal contraction, 6 bookkeeping.
+ */
+int sp_set_stage_timers(sp_spec* s, long long* timers);
 
 /* Tuning knobs of the FP64 path (defaults in parentheses):
  *   kmax (96): Lanczos iteration cap; tol (1e-13): relative residual target;

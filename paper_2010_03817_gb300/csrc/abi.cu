@@ -113,6 +113,53 @@ struct Workspace {
 
 }  // namespace
 
+// work space of the mixed path (per CTA) plus its row buffers
+struct MixSpace {
+  int ctas = 0, rows = 0, m = 0, n = 0;
+  float* Q32 = nullptr;
+  double* Q64 = nullptr;
+  uint8_t* region = nullptr;  // only when the region does not fit in shared memory
+  size_t region_bytes = 0;
+  void* digits = nullptr;     // 7 x rows x Kp BF16 digits of coefficient rows
+  int* erow = nullptr;        // rows
+  double* Frows = nullptr;    // rows x P
+  double* Vrows = nullptr;    // rows x P
+  int* err = nullptr;
+  void release() {
+    cudaFree(Q32); cudaFree(Q64); cudaFree(region); cudaFree(digits); cudaFree(erow);
+    cudaFree(Frows); cudaFree(Vrows); cudaFree(err);
+    Q32 = nullptr; Q64 = nullptr; region = nullptr; digits = nullptr; erow = nullptr;
+    Frows = Vrows = nullptr; err = nullptr;
+    ctas = rows = 0;
+  }
+  int ensure(int n_, int m_, int ctas_, int rows_, int kmax32, int kmax64, bool with_f) {
+    if (ctas >= ctas_ && rows >= rows_ && m == m_ && n == n_ && (!with_f || Frows)) return SP_OK;
+    release();
+    n = n_;
+    m = m_;
+    ctas = ctas_;
+    rows = rows_;
+    const size_t P = (size_t)m * (m + 1) / 2;
+    region_bytes = mixed_region_bytes(m);
+    const bool in_smem = mixed_smem_bytes(n, m, true) <= (size_t)max_smem_optin();
+    bool ok = cudaMalloc(&Q32, sizeof(float) * (size_t)kmax32 * m * ctas) == cudaSuccess &&
+              cudaMalloc(&Q64, sizeof(double) * (size_t)kmax64 * m * ctas) == cudaSuccess &&
+              (in_smem || cudaMalloc(&region, region_bytes * ctas) == cudaSuccess) &&
+              cudaMalloc(&digits, ozaki_row_bytes(rows, n)) == cudaSuccess &&
+              cudaMalloc(&erow, sizeof(int) * rows) == cudaSuccess &&
+              cudaMalloc(&Vrows, sizeof(double) * P * rows) == cudaSuccess &&
+              (!with_f || cudaMalloc(&Frows, sizeof(double) * P * rows) == cudaSuccess) &&
+              cudaMalloc(&err, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      release();
+      return fail(SP_ENOMEM, "mixed-path work space allocation failed%s");
+    }
+    cudaMemset(err, 0, sizeof(int));
+    return SP_OK;
+  }
+};
+
 struct sp_spec {
   int n = 0, m = 0;
   long long P = 0;
@@ -122,6 +169,38 @@ struct sp_spec {
   double tol = 1e-13;
   double sigma_frac = 0.1;
   Workspace ws;  // for the primitive entry points
+  // mixed path: digits of the A stack (tensor-core formation) and FP32 pairs
+  bool mixed_ok = false;
+  uint16_t* Bsl = nullptr;
+  int* ecol = nullptr;
+  float2* Ahl = nullptr;
+  int kmax32 = 96, kmax64 = 96, power_iters = 8;
+  double tol32 = 1e-5, tol64 = 1e-12, delta1 = 2e-4;
+  long long* prof = nullptr;  // optional stage timers (device, ctas x kProfSlots)
+  int learned_iters = 12;
+  // learned warm start
+  sp_mlp* mlp = nullptr;
+  double x_scale = 1.0, t_scale = 1.0, margin = 0.05;
+  MixSpace ms;  // for the primitive entry points
+  MixWork mixwork(const MixSpace& sp_) const {
+    MixWork w;
+    w.Ahl = Ahl;
+    w.Q32 = sp_.Q32;
+    w.Q64 = sp_.Q64;
+    w.region_global = sp_.region;
+    w.region_bytes = sp_.region_bytes;
+    w.kmax32 = kmax32;
+    w.kmax64 = kmax64;
+    w.power_iters = power_iters;
+    w.learned_iters = learned_iters;
+    w.tol32 = tol32;
+    w.tol64 = tol64;
+    w.delta1 = delta1;
+    w.sigma_frac = sigma_frac;
+    w.ctas = sp_.ctas;
+    w.prof = prof;
+    return w;
+  }
   DevSpec dev() const {
     DevSpec d;
     d.n = n;
@@ -143,6 +222,43 @@ struct sp_chains {
   int* status = nullptr;
   long long* stats = nullptr;
   Workspace ws;
+  // mixed path state
+  MixSpace ms;
+  double* F = nullptr;       // C x P carried F(x)
+  bool F_valid = false;
+  double* Xstart = nullptr;  // C x n
+  double* ell = nullptr;
+  double* tprev = nullptr;
+  int* nrefl = nullptr;
+  int* done = nullptr;
+  int* ids[2] = {nullptr, nullptr};
+  double* dirs[2] = {nullptr, nullptr};
+  int* counts = nullptr;     // 2
+  int* h_count = nullptr;    // pinned host mirror
+  float* feats = nullptr;    // C x 2n features of the learned path
+  // optional per-kernel timing of walk calls (CUDA events on the walk's stream)
+  bool timing = false;
+  double t_form_ms = 0.0, t_wave_ms = 0.0, t_mlp_ms = 0.0, t_fp64_ms = 0.0;
+  long long n_form = 0, n_wave = 0, n_mlp = 0, n_fp64 = 0, n_other = 0;
+  // tuple recording (caller buffers)
+  float* rec_x = nullptr;
+  float* rec_y = nullptr;
+  int* rec_count = nullptr;
+  int rec_cap = 0;
+  void release_mixed() {
+    ms.release();
+    cudaFree(F); cudaFree(Xstart); cudaFree(ell); cudaFree(tprev); cudaFree(nrefl);
+    cudaFree(done); cudaFree(ids[0]); cudaFree(ids[1]); cudaFree(dirs[0]); cudaFree(dirs[1]);
+    cudaFree(counts);
+    cudaFree(feats);
+    feats = nullptr;
+    if (h_count) cudaFreeHost(h_count);
+    F = Xstart = ell = tprev = nullptr;
+    nrefl = done = counts = h_count = nullptr;
+    ids[0] = ids[1] = nullptr;
+    dirs[0] = dirs[1] = nullptr;
+    F_valid = false;
+  }
 };
 
 extern "C" {
@@ -205,6 +321,33 @@ int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_sp
     delete s;
     return cuda_fail(e1 != cudaSuccess ? e1 : e2, "sp_create_spectrahedron: upload");
   }
+  // mixed path: BF16 digits of the stack (n + 1 <= kOzakiMaxK) and FP32 pairs
+  if (n + 1 <= kOzakiMaxK && !(flags & 1u)) {
+    const size_t nb = ozaki_b_bytes(P, n);
+    std::vector<uint16_t> bsl(nb / 2);
+    std::vector<int> ecol(P);
+    ozaki_slice_stack(packed.data(), n, P, bsl.data(), ecol.data());
+    std::vector<float2> ahl(packed.size());
+    for (size_t e = 0; e < packed.size(); ++e) {
+      const float h = (float)packed[e];
+      ahl[e] = make_float2(h, (float)(packed[e] - (double)h));
+    }
+    bool ok = cudaMalloc(&s->Bsl, nb) == cudaSuccess &&
+              cudaMalloc(&s->ecol, sizeof(int) * P) == cudaSuccess &&
+              cudaMalloc(&s->Ahl, sizeof(float2) * ahl.size()) == cudaSuccess &&
+              cudaMemcpy(s->Bsl, bsl.data(), nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(s->ecol, ecol.data(), sizeof(int) * P, cudaMemcpyHostToDevice) ==
+                  cudaSuccess &&
+              cudaMemcpy(s->Ahl, ahl.data(), sizeof(float2) * ahl.size(),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaFree(s->Bsl); cudaFree(s->ecol); cudaFree(s->Ahl);
+      s->Bsl = nullptr; s->ecol = nullptr; s->Ahl = nullptr;
+    } else {
+      s->mixed_ok = true;
+    }
+  }
   *out = s;
   return SP_OK;
 }
@@ -213,6 +356,10 @@ int sp_destroy_spectrahedron(sp_spec* s) {
   if (!s) return fail(SP_EINVAL, "sp_destroy_spectrahedron: null handle%s");
   cudaFree(s->A);
   cudaFree(s->pidx);
+  cudaFree(s->Bsl);
+  cudaFree(s->ecol);
+  cudaFree(s->Ahl);
+  s->ms.release();
   s->ws.release();
   delete s;
   return SP_OK;
@@ -236,7 +383,43 @@ int sp_set_solver(sp_spec* s, int kmax, double tol, double sigma_frac) {
 }
 
 static int check_mode(int mode, const char* fn) {
-  if (mode != SP_MODE_FP64) return fail(SP_EINVAL, "%s: unknown mode", fn);
+  if (mode != SP_MODE_FP64 && mode != SP_MODE_MIXED && mode != SP_MODE_LEARNED)
+    return fail(SP_EINVAL, "%s: unknown mode", fn);
+  return SP_OK;
+}
+
+static int check_mixed(const sp_spec* s, const char* fn) {
+  if (!s->mixed_ok)
+    return fail(SP_EINVAL, "%s: the mixed path needs n + 1 <= 224 (tensor-core formation)", fn);
+  return SP_OK;
+}
+
+// F rows (lead 1, x) and / or V rows (lead 0, v) on the tensor cores
+static int form_rows_mixed(sp_spec* s, MixSpace& ms, int count, const double* x,
+                           const double* v, double* F_out, double* V_out, cudaStream_t st) {
+  if (x && F_out) {
+    cudaError_t e = launch_ozaki_form(x, count, s->n, 1.0, s->Bsl, s->ecol, s->P, ms.digits,
+                                      ms.erow, F_out, s->P, ms.err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (F)");
+  }
+  if (v && V_out) {
+    cudaError_t e = launch_ozaki_form(v, count, s->n, 0.0, s->Bsl, s->ecol, s->P, ms.digits,
+                                      ms.erow, V_out, s->P, ms.err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (V)");
+  }
+  return SP_OK;
+}
+
+static int run_prim_mixed(sp_spec* s, PrimParams& pp, void* stream) {
+  if (int r = check_mixed(s, "boundary oracle")) return r;
+  const int ctas = std::min(pp.count, device_sms());
+  int r = s->ms.ensure(s->n, s->m, std::max(ctas, 1), pp.count, s->kmax32, s->kmax64, true);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  r = form_rows_mixed(s, s->ms, pp.count, pp.x, pp.v, s->ms.Frows, s->ms.Vrows, st);
+  if (r) return r;
+  cudaError_t e = launch_prim_mixed(s->dev(), s->mixwork(s->ms), pp, s->ms.Frows, s->ms.Vrows, st);
+  if (e != cudaSuccess) return cuda_fail(e, "mixed boundary-oracle kernel launch");
   return SP_OK;
 }
 
@@ -279,6 +462,7 @@ int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double
   pp.t_plus = t_plus;
   pp.u = u;
   pp.status = status;
+  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, stream);
   return run_prim(s, pp, stream);
 }
 
@@ -298,7 +482,94 @@ int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* 
   pp.w_hat = w_hat;
   pp.s = s_out;
   pp.status = status;
+  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, stream);
   return run_prim(s, pp, stream);
+}
+
+int sp_attach_mlp(sp_spec* s, sp_mlp* q, double x_scale, double t_scale, double margin,
+                  int iters) {
+  if (!s) return fail(SP_EINVAL, "sp_attach_mlp: null handle%s");
+  if (q) {
+    int din = 0, dout = 0;
+    spg_mlp_io(q, &din, &dout);
+    if (din != 2 * s->n || dout != 1 + s->m)
+      return fail(SP_EINVAL, "sp_attach_mlp: the network must map 2n inputs to 1 + m outputs%s");
+    if (!(x_scale > 0.0) || !(t_scale > 0.0) || !(margin > 0.0 && margin < 1.0) || iters < 1)
+      return fail(SP_EINVAL, "sp_attach_mlp: x_scale, t_scale > 0, 0 < margin < 1, iters >= 1%s");
+  }
+  s->mlp = q;
+  s->x_scale = x_scale;
+  s->t_scale = t_scale;
+  s->margin = margin;
+  s->learned_iters = iters;
+  return SP_OK;
+}
+
+int sp_kernel_timing(sp_chains* ch, int enable, double* out) {
+  if (!ch) return fail(SP_EINVAL, "sp_kernel_timing: null handle%s");
+  if (out) {
+    out[0] = ch->t_fp64_ms;
+    out[1] = (double)ch->n_fp64;
+    out[2] = ch->t_form_ms;
+    out[3] = (double)ch->n_form;
+    out[4] = ch->t_wave_ms;
+    out[5] = (double)ch->n_wave;
+    out[6] = ch->t_mlp_ms;
+    out[7] = (double)ch->n_mlp;
+    out[8] = (double)ch->n_other;
+  }
+  if (enable >= 0) {
+    ch->timing = enable != 0;
+    ch->t_fp64_ms = ch->t_form_ms = ch->t_wave_ms = ch->t_mlp_ms = 0.0;
+    ch->n_fp64 = ch->n_form = ch->n_wave = ch->n_mlp = ch->n_other = 0;
+  }
+  return SP_OK;
+}
+
+int sp_record_tuples(sp_chains* ch, float* x_out, float* y_out, int capacity, int* count) {
+  if (!ch) return fail(SP_EINVAL, "sp_record_tuples: null handle%s");
+  if (x_out && (!y_out || !count || capacity < 1))
+    return fail(SP_EINVAL, "sp_record_tuples: buffers, capacity and counter go together%s");
+  ch->rec_x = x_out;
+  ch->rec_y = y_out;
+  ch->rec_count = count;
+  ch->rec_cap = x_out ? capacity : 0;
+  return SP_OK;
+}
+
+int sp_set_stage_timers(sp_spec* s, long long* timers) {
+  if (!s) return fail(SP_EINVAL, "sp_set_stage_timers: null handle%s");
+  s->prof = timers;
+  return SP_OK;
+}
+
+int sp_form_pencil(sp_spec* s, int count, const double* x, const double* v, double* F_out,
+                   double* V_out, int mode, void* stream) {
+  if (!s || count < 0) return fail(SP_EINVAL, "sp_form_pencil: bad argument%s");
+  if ((x == nullptr) != (F_out == nullptr) || (v == nullptr) != (V_out == nullptr))
+    return fail(SP_EINVAL, "sp_form_pencil: x / F_out and v / V_out go together%s");
+  if (int r = check_mode(mode, "sp_form_pencil")) return r;
+  if (count == 0) return SP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == SP_MODE_FP64) {
+    cudaError_t e = cudaSuccess;
+    if (x) e = launch_form64(s->A, s->P, s->n, x, count, 1.0, F_out, s->P, st);
+    if (e == cudaSuccess && v) e = launch_form64(s->A, s->P, s->n, v, count, 0.0, V_out, s->P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sp_form_pencil");
+    return SP_OK;
+  }
+  if (int r = check_mixed(s, "sp_form_pencil")) return r;
+  int r = s->ms.ensure(s->n, s->m, std::min(count, device_sms()), count, s->kmax32, s->kmax64,
+                       true);
+  if (r) return r;
+  r = form_rows_mixed(s, s->ms, count, x, v, F_out, V_out, st);
+  if (r) return r;
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(&herr, s->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sp_form_pencil");
+  if (herr) return fail(SP_ECUDA, "sp_form_pencil: tensor-core wait limit reached%s");
+  return SP_OK;
 }
 
 int sp_init_chains(sp_spec* s, int C, const double* x0, uint64_t seed, uint32_t chain0,
@@ -368,7 +639,159 @@ int sp_destroy_chains(sp_chains* ch) {
   cudaFree(ch->status);
   cudaFree(ch->stats);
   ch->ws.release();
+  ch->release_mixed();
   delete ch;
+  return SP_OK;
+}
+
+static int ensure_chain_mixed(sp_chains* ch) {
+  sp_spec* s = ch->spec;
+  const int C = ch->C, n = s->n;
+  int r = ch->ms.ensure(n, s->m, std::min(C, device_sms()), C, s->kmax32, s->kmax64, false);
+  if (r) return r;
+  if (ch->F) return SP_OK;
+  const size_t P = (size_t)s->P;
+  bool ok = cudaMalloc(&ch->F, sizeof(double) * P * C) == cudaSuccess &&
+            cudaMalloc(&ch->Xstart, sizeof(double) * (size_t)C * n) == cudaSuccess &&
+            cudaMalloc(&ch->ell, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&ch->tprev, sizeof(double) * C) == cudaSuccess &&
+            cudaMalloc(&ch->nrefl, sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&ch->done, sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&ch->ids[0], sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&ch->ids[1], sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&ch->dirs[0], sizeof(double) * (size_t)C * n) == cudaSuccess &&
+            cudaMalloc(&ch->dirs[1], sizeof(double) * (size_t)C * n) == cudaSuccess &&
+            cudaMalloc(&ch->counts, 2 * sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&ch->h_count, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ch->release_mixed();
+    return fail(SP_ENOMEM, "mixed-path chain state allocation failed%s");
+  }
+  ch->F_valid = false;
+  return SP_OK;
+}
+
+// Mixed path: waves of one segment per active chain.  Each wave forms V for
+// the active chains on the tensor cores, then runs the mixed segment kernel,
+// which queues the chains that still have steps to do for the next wave.
+static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rho, double kappa,
+                          bool learned, void* stream) {
+  sp_spec* s = ch->spec;
+  if (int r = check_mixed(s, "walk")) return r;
+  if (learned && !s->mlp)
+    return fail(SP_EINVAL, "walk: the learned mode needs a network (sp_attach_mlp)%s");
+  if (int r = ensure_chain_mixed(ch)) return r;
+  if (learned && !ch->feats &&
+      cudaMalloc(&ch->feats, sizeof(float) * (size_t)ch->C * 2 * s->n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SP_ENOMEM, "walk: feature buffer allocation failed%s");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevSpec ds = s->dev();
+  if (!ch->F_valid) {
+    cudaError_t e = launch_ozaki_form(ch->X, ch->C, s->n, 1.0, s->Bsl, s->ecol, s->P,
+                                      ch->ms.digits, ch->ms.erow, ch->F, s->P, ch->ms.err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (F)");
+    ch->F_valid = true;
+  }
+  MixWave wv{};
+  wv.kind = kind;
+  wv.C = ch->C;
+  wv.steps = steps;
+  wv.rho = rho;
+  wv.step0 = ch->step;
+  wv.chain0 = ch->chain0;
+  wv.seed = ch->seed;
+  wv.tau = tau;
+  wv.kappa = kappa;
+  wv.X = ch->X;
+  wv.Xstart = ch->Xstart;
+  wv.F = ch->F;
+  wv.Vrows = ch->ms.Vrows;
+  wv.ell = ch->ell;
+  wv.tprev = ch->tprev;
+  wv.nrefl = ch->nrefl;
+  wv.done = ch->done;
+  wv.status = ch->status;
+  wv.stats = ch->stats;
+  wv.pred = nullptr;
+  wv.ld_pred = 0;
+  wv.t_scale = s->t_scale;
+  wv.margin = s->margin;
+  wv.x_scale = s->x_scale;
+  wv.rec_x = ch->rec_x;
+  wv.rec_y = ch->rec_y;
+  wv.rec_count = ch->rec_count;
+  wv.rec_cap = ch->rec_cap;
+  int cur = 0;
+  wv.id_cur = ch->ids[0];
+  wv.dir_cur = ch->dirs[0];
+  wv.count_cur = ch->counts;
+  cudaError_t e = launch_mixed_begin(ds, wv, st);
+  if (e != cudaSuccess) return cuda_fail(e, "walk start kernel launch");
+  const MixWork mw = s->mixwork(ch->ms);
+  cudaEvent_t ev[8] = {};
+  if (ch->timing)
+    for (auto& x : ev) cudaEventCreate(&x);
+  ch->n_other += 2;  // start kernel, count copies aside: F formation + start
+  for (long long wave = 0; wave < (1ll << 40); ++wave) {
+    e = cudaMemcpyAsync(ch->h_count, ch->counts + cur, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "walk wave count");
+    const int count = *ch->h_count;
+    if (count <= 0) break;
+    wv.id_cur = ch->ids[cur];
+    wv.dir_cur = ch->dirs[cur];
+    wv.count_cur = ch->counts + cur;
+    wv.id_next = ch->ids[cur ^ 1];
+    wv.dir_next = ch->dirs[cur ^ 1];
+    wv.count_next = ch->counts + (cur ^ 1);
+    e = cudaMemsetAsync(wv.count_next, 0, sizeof(int), st);
+    if (ch->timing) cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess)
+      e = launch_ozaki_form(wv.dir_cur, count, s->n, 0.0, s->Bsl, s->ecol, s->P, ch->ms.digits,
+                            ch->ms.erow, ch->ms.Vrows, s->P, ch->ms.err, st);
+    if (ch->timing) cudaEventRecord(ev[1], st);
+    ch->n_form += 2;  // digit slicing + tensor-core formation
+    if (e == cudaSuccess && learned && kind == 0) {
+      // warm start: the network's (log t+, u) for every listed chain
+      e = launch_learned_features(ch->X, wv.dir_cur, wv.id_cur, count, s->n, s->x_scale,
+                                  ch->feats, st);
+      if (e != cudaSuccess) return cuda_fail(e, "learned features");
+      const float* Y = nullptr;
+      int ld = 0;
+      if (int r = spg_mlp_infer(s->mlp, count, ch->feats, st, &Y, &ld)) return r;
+      wv.pred = Y;
+      wv.ld_pred = ld;
+      ch->n_mlp += 5;  // features, conversion, 3 GEMMs
+    }
+    if (ch->timing) cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = launch_mixed_wave(ds, mw, wv, st);
+    if (ch->timing) cudaEventRecord(ev[3], st);
+    ch->n_wave += 1;
+    if (e != cudaSuccess) return cuda_fail(e, "walk wave launch");
+    cur ^= 1;
+    if (ch->timing) {
+      // the next wave's count copy synchronises the stream; read this wave's events
+      cudaEventSynchronize(ev[3]);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      cudaEventElapsedTime(&a0, ev[0], ev[1]);
+      cudaEventElapsedTime(&a1, ev[1], ev[2]);
+      cudaEventElapsedTime(&a2, ev[2], ev[3]);
+      ch->t_form_ms += a0;
+      ch->t_mlp_ms += a1;
+      ch->t_wave_ms += a2;
+    }
+  }
+  if (ch->timing)
+    for (auto& x : ev) cudaEventDestroy(x);
+  int herr = 0;
+  e = cudaMemcpyAsync(&herr, ch->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "walk");
+  if (herr) return fail(SP_ECUDA, "walk: tensor-core wait limit reached%s");
+  ch->step += (uint32_t)steps;
   return SP_OK;
 }
 
@@ -379,6 +802,9 @@ static int run_walk(sp_chains* ch, int kind, int steps, double tau, int rho, dou
   if (int r = check_mode(mode, fn)) return r;
   if (steps == 0) return SP_OK;
   sp_spec* s = ch->spec;
+  if (mode == SP_MODE_MIXED || mode == SP_MODE_LEARNED)
+    return run_walk_mixed(ch, kind, steps, tau, rho, kappa, mode == SP_MODE_LEARNED, stream);
+  ch->F_valid = false;  // the FP64 path does not maintain the carried F
   const int ctas = std::min(ch->C, device_sms());
   int r = ch->ws.ensure(s->n, s->m, s->kmax, ctas);
   if (r) return r;
@@ -396,8 +822,24 @@ static int run_walk(sp_chains* ch, int kind, int steps, double tau, int rho, dou
   wp.X = ch->X;
   wp.status = ch->status;
   wp.stats = ch->stats;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ch->timing) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, (cudaStream_t)stream);
+  }
   cudaError_t e = launch_walk_fp64(s->dev(), ch->ws.dev(s->tol), wp, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+  ch->n_fp64 += 1;
+  if (ch->timing) {
+    cudaEventRecord(e1, (cudaStream_t)stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ch->t_fp64_ms += ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   ch->step += (uint32_t)steps;
   return SP_OK;
 }
@@ -439,6 +881,7 @@ int sp_set_state(sp_chains* ch, const double* x, uint32_t step, void* stream) {
                           (cudaStream_t)stream));
   if (!is_device_ptr(x)) SP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   ch->step = step;
+  ch->F_valid = false;
   return SP_OK;
 }
 

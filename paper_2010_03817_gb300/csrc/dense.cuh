@@ -13,48 +13,94 @@ namespace spg {
 
 constexpr int kBlk = 32;
 
-// In-place Cholesky G = L L^T of the packed lower triangle G (m x m).
-// col: scratch of m elements.  Returns true on success (CTA-uniform); on
-// failure *fail_col = first column whose pivot was not positive.
+// 1/sqrt(x) and 1/x: an FP32 seed refined by Newton steps in T (FP64 division
+// and square root are long instruction sequences on this GPU's narrow FP64
+// pipe; two Newton steps from 2^-23 reach full double precision)
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) {
+  double r = (double)rsqrtf((float)x);
+  r = r * (1.5 - 0.5 * x * r * r);
+  r = r * (1.5 - 0.5 * x * r * r);
+  return r;
+}
+__device__ __forceinline__ float recip_t(float x) { return 1.0f / x; }
+__device__ __forceinline__ double recip_t(double x) {
+  double r = (double)(1.0f / (float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+}
+
+// In-place Cholesky G = L L^T of the packed lower triangle G (m x m),
+// right-looking in panels of kPanel columns: the panel is factored column by
+// column, then the trailing matrix receives one rank-kPanel update (kPanel
+// FMAs per load and store of G).
+// pan: scratch of kPanel * m elements (the panel, transposed).
+// Returns true on success (CTA-uniform); on failure *flag = 1 + the first
+// column whose pivot was not positive.
+constexpr int kPanel = 4;
 template <typename T>
-__device__ bool factor_cholesky(T* G, int m, T* col, int* flag) {
+__device__ bool factor_cholesky(T* G, int m, T* pan, int* flag) {
   const int tid = threadIdx.x;
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      T d = G[tri(j, j)];
-      if (!(d > T(0))) {
-        *flag = j + 1;
-      } else {
-        T l = sqrt(d);
-        G[tri(j, j)] = l;
-        col[j] = T(1) / l;
+  for (int jb = 0; jb < m; jb += kPanel) {
+    const int nb = min(kPanel, m - jb);
+    // ---- panel: columns jb .. jb+nb-1 -------------------------------------
+    for (int c = 0; c < nb; ++c) {
+      const int j = jb + c;
+      if (tid == 0) {
+        const T dj = G[tri(j, j)];
+        // the FP32 seed of rsqrt_t needs dj inside the FP32 range
+        if (!(dj > T(1e-37)) || !(dj < T(3e37))) {
+          *flag = j + 1;
+        } else {
+          const T r = rsqrt_t(dj);  // 1/l
+          G[tri(j, j)] = dj * r;    // l = sqrt(dj)
+          pan[c * m + j] = r;
+        }
+      }
+      __syncthreads();
+      if (*flag) return false;
+      const T rl = pan[c * m + j];
+      for (int i = j + 1 + tid; i < m; i += SPG_THREADS) {
+        const T v = G[tri(i, j)] * rl;
+        G[tri(i, j)] = v;
+        pan[c * m + i] = v;
+      }
+      __syncthreads();
+      // remaining panel columns: G[i][jb+c2] -= L[i][j] L[jb+c2][j], i >= jb + c2
+      const int rest = nb - 1 - c;
+      if (rest > 0) {
+        const int rows = m - (j + 1);
+        for (int q = tid; q < rows * rest; q += SPG_THREADS) {
+          const int i = j + 1 + q / rest;
+          const int c2 = c + 1 + q % rest;
+          const int k = jb + c2;
+          if (i >= k) G[tri(i, k)] -= pan[c * m + i] * pan[c * m + k];
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
-    if (*flag) return false;
-    const T rl = col[j];
-    for (int i = j + 1 + tid; i < m; i += SPG_THREADS) {
-      T v = G[tri(i, j)] * rl;
-      G[tri(i, j)] = v;
-      col[i] = v;
-    }
-    __syncthreads();
-    // trailing update of rows i > j, columns j < k <= i, flattened so that
-    // every lane of every warp has an element
-    const int s = m - j - 1;
+    // ---- trailing update, rows / columns >= j0: rank-nb --------------------
+    const int j0 = jb + nb;
+    const int s = m - j0;
+    if (s <= 0) break;
     const int total = s * (s + 1) / 2;
     if (tid < total) {
-      int i = j + 1, off = tid;  // element (i, j+1+off)
-      while (off >= i - j) {
-        off -= i - j;
+      int i = j0, off = tid;  // element (i, j0 + off)
+      while (off > i - j0) {
+        off -= i - j0 + 1;
         ++i;
       }
       for (int q = tid; q < total; q += SPG_THREADS) {
-        const int k = j + 1 + off;
-        G[tri(i, k)] -= col[i] * col[k];
+        const int k = j0 + off;
+        T acc = G[tri(i, k)];
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c)
+          if (c < nb) acc -= pan[c * m + i] * pan[c * m + k];
+        G[tri(i, k)] = acc;
         off += SPG_THREADS;
-        while (i < m && off >= i - j) {
-          off -= i - j;
+        while (i < m && off > i - j0) {
+          off -= i - j0 + 1;
           ++i;
         }
       }
@@ -77,13 +123,13 @@ __device__ void invert_diag_blocks(T* L, int m) {
     for (int r = 0; r < bs; ++r) {
       // X[r][c] = -(sum_{k=c}^{r-1} D[r][k] X[k][c]) / D[r][r], X[r][r] = 1/D[r][r]
       T val = T(0);
-      const T drr = L[tri(r0 + r, r0 + r)];
+      const T rdrr = recip_t(L[tri(r0 + r, r0 + r)]);
       if (lane < r) {
         T acc = T(0);
         for (int k = lane; k < r; ++k) acc += L[tri(r0 + r, r0 + k)] * L[tri(r0 + k, r0 + lane)];
-        val = -acc / drr;
+        val = -acc * rdrr;
       } else if (lane == r) {
-        val = T(1) / drr;
+        val = rdrr;
       }
       __syncwarp();
       if (lane <= r) L[tri(r0 + r, r0 + lane)] = val;

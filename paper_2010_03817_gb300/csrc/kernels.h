@@ -3,6 +3,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct sp_mlp;
+// forward pass of the warm-start network on B rows of device features X;
+// *Y receives the device output (B rows, leading dimension *ld)
+int spg_mlp_infer(sp_mlp* q, int B, const float* X, cudaStream_t st, const float** Y, int* ld);
+int spg_mlp_io(const sp_mlp* q, int* din, int* dout);
+
 namespace spg {
 
 // per-chain / per-item status words (mirrored by SP_ST_* in spectra_gb.h)
@@ -23,7 +29,11 @@ enum StatSlot : int {
   kStatLanczos = 3,      // Lanczos iterations
   kStatShiftRetry = 4,   // shifted factorisations that failed and were redone unshifted
   kStatNoConv = 5,       // eigen-solves that hit the iteration cap
-  kNumStats = 8,
+  kStatFallback = 6,     // mixed path: FP64 Lanczos fallbacks
+  kStatPower = 7,        // mixed path: FP64 power iterations
+  kStatLearnedOk = 8,    // learned path: warm starts accepted by the certificate
+  kStatLearnedMiss = 9,  // learned path: warm starts rejected (plain stage 1 instead)
+  kNumStats = 12,
 };
 
 struct DevSpec {
@@ -73,6 +83,94 @@ struct PrimParams {
 };
 
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem);
+
+// ---- mixed-precision path ----------------------------------------------------
+struct MixWork {
+  const float2* Ahl;        // (n+1) x P: the A stack as FP32 (hi, lo) pairs
+  float* Q32;               // per CTA: kmax32 * m (FP32 Lanczos basis)
+  double* Q64;              // per CTA: kmax64 * m (FP64 fallback basis)
+  uint8_t* region_global;   // per CTA work region when it does not fit in shared memory
+  size_t region_bytes;
+  int kmax32, kmax64, power_iters, learned_iters;
+  double tol32, tol64, delta1, sigma_frac;
+  int ctas;
+  long long* prof;  // optional: per-CTA clock64 sums per stage (kProfSlots each)
+};
+constexpr int kProfSlots = 8;
+
+struct MixWave {
+  int kind, C, steps, rho;
+  uint32_t step0, chain0;
+  uint64_t seed;
+  double tau, kappa;
+  double* X;        // C x n current points
+  double* Xstart;   // C x n start of the current step
+  double* F;        // C x P carried F(x) (FP64 packed)
+  const double* Vrows;  // count x P: V of the listed chains (FP64 packed)
+  double* ell;      // C remaining Billiard length
+  double* tprev;    // C previous t+ (0 at a step start)
+  int* nrefl;       // C reflections in the current step
+  int* done;        // C steps completed in this call
+  int* id_cur;      // active chains of this wave
+  double* dir_cur;  // their directions (count x n)
+  int* count_cur;
+  int* id_next;
+  double* dir_next;
+  int* count_next;
+  int* status;
+  long long* stats;
+  // learned warm start: predictions for the listed chains (row r: log(t/t_scale), u)
+  const float* pred;
+  int ld_pred;
+  double t_scale, margin;
+  // recording of (features, targets) tuples for training
+  float* rec_x;     // cap x 2n: (x * x_scale, v)
+  float* rec_y;     // cap x (1 + m): (log(t+ / t_scale), u)
+  int* rec_count;
+  int rec_cap;
+  double x_scale;
+};
+
+size_t mixed_region_bytes(int m);
+cudaError_t launch_learned_features(const double* X, const double* dir, const int* id, int count,
+                                    int n, double x_scale, float* feats, cudaStream_t st);
+size_t mixed_smem_bytes(int n, int m, bool region_in_smem);
+cudaError_t launch_mixed_begin(const DevSpec& sp, const MixWave& wv, cudaStream_t st);
+cudaError_t launch_mixed_wave(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
+                              cudaStream_t st);
+cudaError_t launch_prim_mixed(const DevSpec& sp, const MixWork& mw, const PrimParams& pp,
+                              const double* Frows, const double* Vrows, cudaStream_t st);
+
+// pencil formation: Y[r, :] = lead * A_0 + sum_j vec[r, j] A_{j+1} (packed)
+cudaError_t launch_form64(const double* A, long long P, int n, const double* vec, int R,
+                          double lead, double* Y, long long ldy, cudaStream_t st);
+// the same on the BF16 tensor cores with the exact digit splitting
+int ozaki_kp(int n);
+size_t ozaki_b_bytes(long long P, int n);
+size_t ozaki_row_bytes(int R, int n);
+void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol);
+cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const uint16_t* Bsl,
+                              const int* ecol, long long P, void* row_digits, int* erow,
+                              double* Y, long long ldy, int* err, cudaStream_t st);
+constexpr int kOzakiMaxK = 224;  // n + 1 limit of the tensor-core formation
+
+// BF16 GEMM on tcgen05: C = A B^T (+ bias) (ReLU); FP32 and / or BF16 output
+cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                             const float* bias, int relu, float* C32, int ldc32, void* C16,
+                             int ldc16, int* err, cudaStream_t st);
+// MLP helpers (mlp.cu)
+cudaError_t launch_f32_to_bf16(const float* in, void* out, long long n, cudaStream_t st);
+cudaError_t launch_f32_to_bf16_pad(const float* in, int B, int din, int dinp, void* out,
+                                   cudaStream_t st);
+cudaError_t launch_transpose_bf16(const void* in, int R, int C, int ldi, void* out, int ldo,
+                                  cudaStream_t st);
+cudaError_t launch_loss_grad(const float* Y, const float* T, int B, int D, int ld, void* dY16,
+                             float* loss_acc, cudaStream_t st);
+cudaError_t launch_relu_back(void* dH, const void* H, long long n, cudaStream_t st);
+cudaError_t launch_col_sum(const void* dZ, int R, int C, int ld, float* g, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, long long n, float lr,
+                        float b1, float b2, float c1, float c2, float eps, void* p16, void* pt16,
+                        int rows, int cols, cudaStream_t st);
 cudaError_t launch_walk_fp64(const DevSpec& sp, const DevWork& wk, const WalkParams& wp,
                              cudaStream_t st);
 cudaError_t launch_prim_fp64(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,

@@ -5,8 +5,11 @@
 // det(F(x) + t V) as t = sigma + 1/mu: the largest mu gives t+ (Sec. 2.3,
 // Lemma "PEP and S cap C"), the smallest gives t-.
 //
-// The small tridiagonal matrix T_K is analysed by multisection on Sturm
-// counts (one warp) and inverse iteration (one thread), both in FP64.
+// The small tridiagonal matrix T_K is analysed in FP32 (multisection on
+// Sturm counts by one warp, inverse iteration by one thread) for the
+// convergence tests; FP64 inverse iteration, shifted by its own Rayleigh
+// quotient, gives the final Ritz pairs (and the tests of the FP64 solve once
+// the FP32 residual estimate reaches its floor).
 #pragma once
 #include "common.cuh"
 #include "dense.cuh"
@@ -24,8 +27,12 @@ struct LanczosScalars {
   double cwork[kMaxLanczos];
   double h[kMaxLanczos];
   double red[SPG_WARPS];
+  float af[kMaxLanczos];         // FP32 copies of alpha, beta and beta^2 (cheap analysis)
+  float bf[kMaxLanczos + 1];
+  float b2f[kMaxLanczos + 1];
+  float sf[2 * kMaxLanczos];     // FP32 Ritz coefficients + Thomas scratch
   double theta_max, theta_min, res_max, res_min;
-  int K, done, flag;
+  int K, done, flag, precise;
 };
 
 // Sturm count: number of eigenvalues of T below x
@@ -41,9 +48,60 @@ __device__ __forceinline__ int sturm_count(const double* a, const double* b, int
   return c;
 }
 
+// FP32 Sturm count (cheap: FP32 pipe)
+__device__ __forceinline__ int sturm_count_f(const float* a, const float* b2, int K, float x) {
+  const float tiny = 1e-30f;
+  float d = a[0] - x;
+  int c = d < 0.f;
+  for (int i = 1; i < K; ++i) {
+    if (fabsf(d) < tiny) d = d < 0.f ? -tiny : tiny;
+    d = (a[i] - x) - b2[i] / d;
+    c += d < 0.f;
+  }
+  return c;
+}
+
+// warp 0: FP32 estimate (relative width ~1e-6) of the largest (want_max) or
+// smallest eigenvalue of T_K; af / b2f hold the FP32 diagonal and squared
+// off-diagonal
+__device__ inline float tri_extreme_f(const float* af, const float* b2f, int K, bool want_max) {
+  const int lane = threadIdx.x & 31;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  for (int i = lane; i < K; i += 32) {
+    const float r = (i > 0 ? sqrtf(b2f[i]) : 0.f) + (i + 1 < K ? sqrtf(b2f[i + 1]) : 0.f);
+    lo = fminf(lo, af[i] - r);
+    hi = fmaxf(hi, af[i] + r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const float span = fmaxf(hi - lo, 1e-30f);
+  lo -= 1e-3f * span;
+  hi += 1e-3f * span;
+  for (int round = 0; round < 12; ++round) {
+    const float w = hi - lo;
+    if (!(w > 4e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
+    const float x = lo + (float)(lane + 1) * (w / 33.f);
+    const int c = sturm_count_f(af, b2f, K, x);
+    const bool below = want_max ? (c <= K - 1) : (c == 0);
+    const unsigned mb = __ballot_sync(0xffffffffu, below);
+    const unsigned ma = ~mb;
+    const int lb = mb ? 31 - __clz(mb) : -1;
+    const int la = ma ? __ffs(ma) - 1 : 32;
+    const float nlo = lb >= 0 ? __shfl_sync(0xffffffffu, x, lb) : lo;
+    const float nhi = la < 32 ? __shfl_sync(0xffffffffu, x, la) : hi;
+    if (!(nlo < nhi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  return 0.5f * (lo + hi);
+}
+
 // warp 0: the largest (want_max) or smallest eigenvalue of T_K by 33-way
 // multisection on Sturm counts, to a relative width of ~1e-15
-__device__ double tri_extreme(const double* a, const double* b, int K, bool want_max) {
+__device__ inline double tri_extreme(const double* a, const double* b, int K, bool want_max) {
   const int lane = threadIdx.x & 31;
   double lo = 1.0e308, hi = -1.0e308;
   for (int i = lane; i < K; i += 32) {
@@ -79,6 +137,17 @@ __device__ double tri_extreme(const double* a, const double* b, int K, bool want
   return 0.5 * (lo + hi);
 }
 
+// 1/x in FP64 from an FP32 seed and two Newton steps (quadratic convergence:
+// 2^-23 -> 2^-46 -> below 2^-53); x is never 0 here (pivots are guarded)
+__device__ __forceinline__ double recip64(double x) {
+  double r = (double)(1.0f / (float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+}
+__device__ __forceinline__ float recip_any(float x) { return 1.0f / x; }
+__device__ __forceinline__ double recip_any(double x) { return recip64(x); }
+
 // thread 0: inverse iteration on (T - theta I) for the eigenvector s (two
 // passes, Thomas algorithm with guarded pivots).  Returns the Rayleigh
 // quotient s^T T s / s^T s and writes the normalised s.
@@ -88,18 +157,21 @@ __device__ R tri_eigvec(const double* a, const double* b, int K, R theta, R* s, 
   const R eps = (sizeof(R) == 8) ? R(2.2e-16) : R(1.2e-7);
   R scale = R(0);
   for (int i = 0; i < K; ++i) scale = fmax(scale, fabs((R)a[i] - theta) + fabs((R)b[i]));
-  const R guard = fmax(eps * scale, tiny);
+  // the FP32 seed of recip64 needs a guard inside the FP32 range
+  const R guard = fmax(eps * scale, (sizeof(R) == 8) ? R(1e-30) : tiny);
   for (int i = 0; i < K; ++i) s[i] = R(1);
   for (int pass = 0; pass < 2; ++pass) {
     R den = (R)a[0] - theta;
     if (fabs(den) < guard) den = den < R(0) ? -guard : guard;
-    cw[0] = (K > 1 ? (R)b[1] : R(0)) / den;
-    s[0] = s[0] / den;
+    R rd = recip_any(den);
+    cw[0] = (K > 1 ? (R)b[1] : R(0)) * rd;
+    s[0] = s[0] * rd;
     for (int i = 1; i < K; ++i) {
       den = ((R)a[i] - theta) - (R)b[i] * cw[i - 1];
       if (fabs(den) < guard) den = den < R(0) ? -guard : guard;
-      cw[i] = (i + 1 < K ? (R)b[i + 1] : R(0)) / den;
-      s[i] = (s[i] - (R)b[i] * s[i - 1]) / den;
+      rd = recip_any(den);
+      cw[i] = (i + 1 < K ? (R)b[i + 1] : R(0)) * rd;
+      s[i] = (s[i] - (R)b[i] * s[i - 1]) * rd;
     }
     for (int i = K - 2; i >= 0; --i) s[i] -= cw[i] * s[i + 1];
     // scale by the largest entry first (the solve may produce huge values)
@@ -109,17 +181,71 @@ __device__ R tri_eigvec(const double* a, const double* b, int K, R theta, R* s, 
       for (int i = 0; i < K; ++i) s[i] = (i == K - 1) ? R(1) : R(0);
       mx = R(1);
     }
-    for (int i = 0; i < K; ++i) s[i] /= mx;
+    const R rmx = R(1) / mx;
     R nrm = R(0);
-    for (int i = 0; i < K; ++i) nrm += s[i] * s[i];
-    nrm = sqrt(nrm);
-    for (int i = 0; i < K; ++i) s[i] /= nrm;
+    for (int i = 0; i < K; ++i) {
+      s[i] *= rmx;
+      nrm += s[i] * s[i];
+    }
+    const R rn = R(1) / sqrt(nrm);
+    for (int i = 0; i < K; ++i) s[i] *= rn;
   }
   R rq = R(0);
   for (int i = 0; i < K; ++i) {
     R ts = (R)a[i] * s[i];
     if (i > 0) ts += (R)b[i] * s[i - 1];
     if (i + 1 < K) ts += (R)b[i + 1] * s[i + 1];
+    rq += s[i] * ts;
+  }
+  return rq;
+}
+
+// eigenpair of T_K near theta to full FP64 accuracy: inverse iteration at the
+// estimate, then again at the Rayleigh quotient it returns
+__device__ inline double tri_eigpair64(const double* a, const double* b, int K, double theta,
+                                       double* s, double* cw) {
+  const double rq = tri_eigvec<double>(a, b, K, theta, s, cw);
+  return tri_eigvec<double>(a, b, K, rq, s, cw);
+}
+
+// FP32 inverse iteration on the FP32 copies (a, b): same scheme as tri_eigvec
+__device__ inline float tri_eigvec_f(const float* a, const float* b, int K, float theta, float* s,
+                                     float* cw) {
+  float scale = 0.f;
+  for (int i = 0; i < K; ++i) scale = fmaxf(scale, fabsf(a[i] - theta) + fabsf(b[i]));
+  const float guard = fmaxf(1.2e-7f * scale, 1e-30f);
+  for (int i = 0; i < K; ++i) s[i] = 1.f;
+  for (int pass = 0; pass < 2; ++pass) {
+    float den = a[0] - theta;
+    if (fabsf(den) < guard) den = den < 0.f ? -guard : guard;
+    cw[0] = (K > 1 ? b[1] : 0.f) / den;
+    s[0] = s[0] / den;
+    for (int i = 1; i < K; ++i) {
+      den = (a[i] - theta) - b[i] * cw[i - 1];
+      if (fabsf(den) < guard) den = den < 0.f ? -guard : guard;
+      cw[i] = (i + 1 < K ? b[i + 1] : 0.f) / den;
+      s[i] = (s[i] - b[i] * s[i - 1]) / den;
+    }
+    for (int i = K - 2; i >= 0; --i) s[i] -= cw[i] * s[i + 1];
+    float mx = 0.f;
+    for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(s[i]));
+    if (!(mx > 0.f) || !isfinite(mx)) {
+      for (int i = 0; i < K; ++i) s[i] = (i == K - 1) ? 1.f : 0.f;
+      mx = 1.f;
+    }
+    float nrm = 0.f;
+    for (int i = 0; i < K; ++i) {
+      s[i] /= mx;
+      nrm += s[i] * s[i];
+    }
+    nrm = sqrtf(nrm);
+    for (int i = 0; i < K; ++i) s[i] /= nrm;
+  }
+  float rq = 0.f;
+  for (int i = 0; i < K; ++i) {
+    float ts = a[i] * s[i];
+    if (i > 0) ts += b[i] * s[i - 1];
+    if (i + 1 < K) ts += b[i + 1] * s[i + 1];
     rq += s[i] * ts;
   }
   return rq;
@@ -170,11 +296,14 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
   {
     T p = T(0);
     for (int i = tid; i < m; i += SPG_THREADS) p += q[i] * q[i];
-    double nrm = sqrt((double)block_sum(p, (T*)sc->red));
-    for (int i = tid; i < m; i += SPG_THREADS) q[i] = (T)(q[i] / nrm);
+    const T rn = T(1) / sqrt(block_sum(p, (T*)sc->red));
+    for (int i = tid; i < m; i += SPG_THREADS) q[i] *= rn;
     if (tid == 0) {
       sc->done = 0;
+      sc->precise = 0;
       sc->beta[0] = 0.0;
+      sc->bf[0] = 0.f;
+      sc->b2f[0] = 0.f;
     }
     __syncthreads();
   }
@@ -183,32 +312,53 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
     T* Qk = Q + (size_t)k * m;
     for (int i = tid; i < m; i += SPG_THREADS) Qk[i] = q[i];
     apply_pencil(op, q, r, z, m, s);
-    // two passes of classical Gram-Schmidt against Q[0..k]
+    // two passes of classical Gram-Schmidt against Q[0..k]; the coefficients
+    // are kept in T (a double -> float conversion runs on the FP64 pipe)
+    T* hT = reinterpret_cast<T*>(sc->h);
     double alpha = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
       for (int j = wid; j <= k; j += SPG_WARPS) {
         const T* Qj = Q + (size_t)j * m;
-        T acc = T(0);
-        for (int i = lane; i < m; i += 32) acc += Qj[i] * r[i];
-        acc = warp_sum(acc);
-        if (lane == 0) sc->h[j] = (double)acc;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int i = lane;
+        for (; i + 96 < m; i += 128) {
+          a0 += Qj[i] * r[i];
+          a1 += Qj[i + 32] * r[i + 32];
+          a2 += Qj[i + 64] * r[i + 64];
+          a3 += Qj[i + 96] * r[i + 96];
+        }
+        for (; i < m; i += 32) a0 += Qj[i] * r[i];
+        const T acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) hT[j] = acc;
       }
       __syncthreads();
       for (int i = tid; i < m; i += SPG_THREADS) {
-        T acc = T(0);
-        for (int j = 0; j <= k; ++j) acc += (T)sc->h[j] * Q[(size_t)j * m + i];
-        r[i] -= acc;
+        // four independent loads in flight per step
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int j = 0;
+        for (; j + 3 <= k; j += 4) {
+          a0 += hT[j] * Q[(size_t)j * m + i];
+          a1 += hT[j + 1] * Q[(size_t)(j + 1) * m + i];
+          a2 += hT[j + 2] * Q[(size_t)(j + 2) * m + i];
+          a3 += hT[j + 3] * Q[(size_t)(j + 3) * m + i];
+        }
+        for (; j <= k; ++j) a0 += hT[j] * Q[(size_t)j * m + i];
+        r[i] -= (a0 + a1) + (a2 + a3);
       }
-      alpha += sc->h[k];
+      alpha += (double)hT[k];
       __syncthreads();
     }
     T p = T(0);
     for (int i = tid; i < m; i += SPG_THREADS) p += r[i] * r[i];
-    const double beta = sqrt((double)block_sum(p, (T*)sc->red));
+    const T beta_t = sqrt(block_sum(p, (T*)sc->red));
+    const double beta = (double)beta_t;
     K = k + 1;
     if (tid == 0) {
       sc->alpha[k] = alpha;
       sc->beta[K] = beta;
+      sc->af[k] = (float)alpha;
+      sc->bf[K] = (float)beta;
+      sc->b2f[K] = (float)(beta * beta);
     }
     __syncthreads();
     // convergence test every few steps (and on breakdown / last step)
@@ -217,36 +367,72 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
     const bool check = breakdown || K == kmax || (K >= 6 && (K % 4 == 0));
     if (check) {
       if (wid == 0) {
-        double tmax = tri_extreme(sc->alpha, sc->beta, K, true);
-        double tmin = want_min ? tri_extreme(sc->alpha, sc->beta, K, false) : 0.0;
+        // FP32 analysis first; the FP64 inverse iteration only once the FP32
+        // residual estimate has reached its floor (or for the final answer)
+        const float tmaxf = tri_extreme_f(sc->af, sc->b2f, K, true);
+        const float tminf = want_min ? tri_extreme_f(sc->af, sc->b2f, K, false) : 0.f;
         if (lane == 0) {
-          double th = tri_eigvec<double>(sc->alpha, sc->beta, K, tmax, sc->s_max, sc->cwork);
-          double resmax = fabs(beta * sc->s_max[K - 1]);
-          double thn = 0.0, resmin = 0.0;
+          const double eps_t = sizeof(T) == 8 ? 2.2e-16 : 1.2e-7;
+          float* sfv = sc->sf;
+          float* cwf = sc->sf + kMaxLanczos;
+          const float thf = tri_eigvec_f(sc->af, sc->bf, K, tmaxf, sfv, cwf);
+          const float rmf = fabsf((float)beta * sfv[K - 1]);
+          float thnf = 0.f, rnf = 0.f;
           if (want_min) {
-            thn = tri_eigvec<double>(sc->alpha, sc->beta, K, tmin, sc->s_min, sc->cwork);
-            resmin = fabs(beta * sc->s_min[K - 1]);
+            thnf = tri_eigvec_f(sc->af, sc->bf, K, tminf, sfv, cwf);
+            rnf = fabsf((float)beta * sfv[K - 1]);
           }
-          const double big = fmax(fabs(th), fabs(thn));
-          // attainable accuracy: the operator is applied with relative error ~ eps |T|
-          const double floor_ = 64.0 * (sizeof(T) == 8 ? 2.2e-16 : 1.2e-7) * big;
-          bool ok = resmax <= fmax(tol * fabs(th), floor_);
-          if (want_min) ok = ok && resmin <= fmax(tol * fabs(thn), floor_);
-          sc->theta_max = th;
-          sc->theta_min = thn;
-          sc->res_max = resmax;
-          sc->res_min = resmin;
+          const float bigf = fmaxf(fabsf(thf), fabsf(thnf));
+          const float floor32 = 64.f * 1.2e-7f * bigf;
+          const float floorT = (float)(64.0 * eps_t) * bigf;
+          bool ok32 = rmf <= fmaxf((float)tol * fabsf(thf), floorT);
+          if (want_min) ok32 = ok32 && rnf <= fmaxf((float)tol * fabsf(thnf), floorT);
+          bool at_floor = rmf <= 4.f * floor32 && (!want_min || rnf <= 4.f * floor32);
+          bool ok = false;
+          if (sizeof(T) == 4 || (double)tol >= 1e-6) {
+            ok = ok32;
+          } else if (at_floor || breakdown || K == kmax) {
+            // FP64 residual estimate: inverse iteration at the FP32 estimate
+            sc->precise = 1;
+            double th = tri_eigpair64(sc->alpha, sc->beta, K, (double)thf, sc->s_max,
+                                            sc->cwork);
+            const double rm = fabs(beta * sc->s_max[K - 1]);
+            double thn = 0.0, rn = 0.0;
+            if (want_min) {
+              thn = tri_eigpair64(sc->alpha, sc->beta, K, (double)thnf, sc->s_min, sc->cwork);
+              rn = fabs(beta * sc->s_min[K - 1]);
+            }
+            const double big = fmax(fabs(th), fabs(thn));
+            const double floor_ = 64.0 * eps_t * big;
+            ok = rm <= fmax(tol * fabs(th), floor_);
+            if (want_min) ok = ok && rn <= fmax(tol * fabs(thn), floor_);
+            sc->theta_max = th;
+            sc->theta_min = thn;
+          }
+          if (!sc->precise) {
+            sc->theta_max = thf;
+            sc->theta_min = thnf;
+          }
           sc->done = (ok || breakdown) ? 2 : (K == kmax ? 1 : 0);
         }
       }
       __syncthreads();
       if (sc->done) break;
     }
-    for (int i = tid; i < m; i += SPG_THREADS) q[i] = (T)(r[i] / beta);
+    {
+      const T rb = T(1) / beta_t;
+      for (int i = tid; i < m; i += SPG_THREADS) q[i] = r[i] * rb;
+    }
     __syncthreads();
   }
-  // the last check left the FP64 Ritz coefficients in s_max / s_min
-  if (tid == 0) sc->K = K;
+  // final Ritz pairs: FP64 inverse iteration at the last estimate (also the
+  // FP64 Rayleigh quotient of T_K)
+  if (tid == 0) {
+    sc->theta_max = tri_eigpair64(sc->alpha, sc->beta, K, sc->theta_max, sc->s_max, sc->cwork);
+    if (want_min)
+      sc->theta_min = tri_eigpair64(sc->alpha, sc->beta, K, sc->theta_min, sc->s_min, sc->cwork);
+    sc->K = K;
+  }
   __syncthreads();
   for (int i = tid; i < m; i += SPG_THREADS) {
     double a = 0.0, b = 0.0;

@@ -1,0 +1,260 @@
+// FP64-quality formation of the pencil matrices on the BF16 tensor cores.
+//
+// For R coefficient rows c_r (length n+1) the kernel computes
+//   Y[r, p] = sum_j c_r[j] A[j, p]            (A: packed LMI stack, (n+1) x P)
+// i.e. V = sum v_j A_j (rows c = (0, v)) and F(x) = A_0 + sum x_j A_j (rows
+// c = (1, x)) -- the pencil B_0 + t B_1 of a line (Lemma "PEP and S cap C").
+//
+// Exactness scheme (error-free splitting of both operands into integer
+// digits, the Ozaki scheme; Ozaki, Ogita, Oishi, Rump 2012, and its
+// tensor-core form, Mukunoki, Ozaki, Ogita, Imamura 2020):
+//   c_r[j] = 2^{f_r} sum_s a_s[r, j] 2^{-7(s+1)},  A[j, p] = 2^{e_p} sum_t b_t[j, p] 2^{-7(t+1)}
+// with integer digits |a_s|, |b_t| <= 64 (exact in BF16), S = 7 digits (49
+// bits).  For each digit-sum d = s + t <= 6 the tensor core accumulates
+//   G_d[r, p] = sum_{s+t=d} sum_j a_s[r, j] b_t[j, p]
+// in FP32 in TMEM; every partial sum is an integer below 7 * 208 * 2^12 < 2^24,
+// so the accumulation is exact.  The epilogue combines the seven integers in
+// 64-bit integer arithmetic and scales once into FP64:
+//   Y = 2^{f_r + e_p} sum_d G_d 2^{-7(d+2)}.
+// The truncation (pairs with s + t > 6, digits beyond the 7th) is below
+// (n+1) 2^-44 max_j |c_r[j]| max_j |A[j, p]|.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace spg {
+namespace {
+
+constexpr int kDigits = 7;        // S
+constexpr int kDigitBits = 7;     // beta
+constexpr int kTileM = 128;       // coefficient rows per CTA
+constexpr int kTileN = 32;        // packed entries per CTA
+constexpr int kGroups = kDigits;  // d = 0..6
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ uint32_t core_off(int r, int g, int kgroups) {
+  return (uint32_t)(((r >> 3) * kgroups + g) * 128 + (r & 7) * 16);
+}
+
+// one warp per row: exponent and digits of c_r = (lead, vec[r, 0..n-1])
+__global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, double lead,
+                                  int Kp, __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= R) return;
+  const double* row = vec + (size_t)r * n;
+  double mx = fabs(lead);
+  for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(row[j]));
+  mx = warp_max(mx);
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);  // mx < 2^e
+    e += 1;         // |c| <= 2^(e-1): normalised values in [-1/2, 1/2]
+  }
+  if (lane == 0) ex[r] = e;
+  for (int k = lane; k < Kp; k += 32) {
+    double y = 0.0;
+    if (k == 0)
+      y = lead;
+    else if (k <= n)
+      y = row[k - 1];
+    y = ldexp(y, -e);
+#pragma unroll
+    for (int s = 0; s < kDigits; ++s) {
+      y *= 128.0;
+      const double d = rint(y);
+      y -= d;
+      out[((size_t)s * R + r) * Kp + k] = __float2bfloat16_rn((float)d);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_form_kernel(const __nv_bfloat16* __restrict__ Asl, const int* __restrict__ erow, int R,
+                      const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ ecol,
+                      long long P, int Kp, double* __restrict__ Y, long long ldy, int* err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int kgroups = Kp / 8;
+  const uint32_t a_bytes = kTileM * Kp * 2;
+  const uint32_t b_bytes = kTileN * Kp * 2;
+  uint8_t* sB = smem;                        // kDigits x [32 x Kp]
+  uint8_t* sA0 = sB + kDigits * b_bytes;     // [128 x Kp], double buffered
+  uint8_t* sA1 = sA0 + a_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA1 + a_bytes);  // 2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+  const long long p0 = (long long)blockIdx.x * kTileN;
+  const int r0 = blockIdx.y * kTileM;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (wid == 0) {
+    tc::tmem_alloc(tmem_slot, 256);
+    tc::tmem_relinquish();
+  }
+  // B digits of this column tile (all of them stay resident)
+  for (int t = 0; t < kDigits; ++t) {
+    uint8_t* dst = sB + t * b_bytes;
+    for (int q = tid; q < kTileN * kgroups; q += kThreads) {
+      const int r = q / kgroups, g = q % kgroups;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (p0 + r < P)
+        v = *reinterpret_cast<const uint4*>(Bsl + ((size_t)t * P + p0 + r) * Kp + g * 8);
+      *reinterpret_cast<uint4*>(dst + core_off(r, g, kgroups)) = v;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
+  const uint32_t sbo = (uint32_t)kgroups * 128;
+  bool ok = true;
+
+  for (int s = 0; s < kDigits; ++s) {
+    const int buf = s & 1;
+    uint8_t* sA = buf ? sA1 : sA0;
+    if (s >= 2 && !tc::mbar_wait(&mbar[buf], ((s - 2) >> 1) & 1)) {
+      ok = false;
+      break;
+    }
+    for (int q = tid; q < kTileM * kgroups; q += kThreads) {
+      const int r = q / kgroups, g = q % kgroups;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (r0 + r < R)
+        v = *reinterpret_cast<const uint4*>(Asl + ((size_t)s * R + r0 + r) * Kp + g * 8);
+      *reinterpret_cast<uint4*>(sA + core_off(r, g, kgroups)) = v;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a_base = tc::smem_u32(sA);
+      for (int t = 0; t + s < kGroups; ++t) {
+        const uint32_t b_base = tc::smem_u32(sB + t * b_bytes);
+        const uint32_t d_tmem = tmem + (uint32_t)((s + t) * kTileN);
+        for (int ks = 0; ks < Kp / 16; ++ks) {
+          const uint64_t ad = tc::smem_desc(a_base + ks * 256, 128, sbo);
+          const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, sbo);
+          tc::mma_bf16(d_tmem, ad, bd, idesc, (s > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&mbar[buf]);
+    }
+  }
+  // the commit of the last digit covers every MMA issued before it
+  if (ok) ok = tc::mbar_wait(&mbar[(kDigits - 1) & 1], ((kDigits - 1) >> 1) & 1);
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // let in-flight MMAs drain (bounded) before the TMEM is released
+    tc::mbar_wait(&mbar[(kDigits - 1) & 1], ((kDigits - 1) >> 1) & 1, 1ll << 20);
+  }
+  tc::fence_after_sync();
+  if (ok) {
+    const int r = r0 + wid * 32 + lane;
+    const int er = (r < R) ? erow[r] : 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(wid * 32) << 16);
+    for (int c0 = 0; c0 < kTileN; c0 += 16) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+#pragma unroll
+      for (int d = 0; d < kGroups; ++d) {
+        uint32_t v[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(d * kTileN + c0), v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const long long g = (long long)__float2ll_rn(__uint_as_float(v[i]));
+          if (d <= 3)
+            hi[i] = hi[i] * (1ll << kDigitBits) + g;
+          else
+            lo[i] = lo[i] * (1ll << kDigitBits) + g;
+        }
+      }
+      if (r < R) {
+        double* yrow = Y + (size_t)r * ldy;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const long long p = p0 + c0 + i;
+          if (p < P) {
+            const int e = er + ecol[p];
+            // hi carries digit sums d = 0..3 (weight 2^{-7(d+2)} = 2^{7(3-d) - 35}),
+            // lo carries d = 4..6 (2^{7(6-d) - 56})
+            yrow[p] = ldexp((double)hi[i], e - 35) + ldexp((double)lo[i], e - 56);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (wid == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+size_t ozaki_b_bytes(long long P, int n) {
+  const int Kp = ((n + 1) + 15) / 16 * 16;
+  return (size_t)kDigits * (size_t)P * Kp * 2;
+}
+
+int ozaki_kp(int n) { return ((n + 1) + 15) / 16 * 16; }
+
+// host: digits of the A stack, column by column (packed entry p over j = 0..n)
+void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol) {
+  const int Kp = ozaki_kp(n);
+  for (long long p = 0; p < P; ++p) {
+    double mx = 0.0;
+    for (int j = 0; j <= n; ++j) mx = fmax(mx, fabs(packed[(size_t)j * P + p]));
+    int e = 0;
+    if (mx > 0.0) {
+      frexp(mx, &e);
+      e += 1;
+    }
+    ecol[p] = e;
+    for (int k = 0; k < Kp; ++k) {
+      double y = (k <= n) ? ldexp(packed[(size_t)k * P + p], -e) : 0.0;
+      for (int s = 0; s < kDigits; ++s) {
+        y *= 128.0;
+        const double d = rint(y);
+        y -= d;
+        // |d| <= 64: the float is exact and its upper 16 bits are the BF16
+        const float f = (float)d;
+        uint32_t bits;
+        memcpy(&bits, &f, 4);
+        Bsl[((size_t)s * P + p) * Kp + k] = (uint16_t)(bits >> 16);
+      }
+    }
+  }
+}
+
+size_t ozaki_row_bytes(int R, int n) { return (size_t)kDigits * R * ozaki_kp(n) * 2; }
+
+cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const uint16_t* Bsl,
+                              const int* ecol, long long P, void* row_digits, int* erow,
+                              double* Y, long long ldy, int* err, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const int Kp = ozaki_kp(n);
+  __nv_bfloat16* Asl = static_cast<__nv_bfloat16*>(row_digits);
+  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, lead, Kp, Asl, erow);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)kDigits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
+  e = cudaFuncSetAttribute(ozaki_form_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((P + kTileN - 1) / kTileN), (unsigned)((R + kTileM - 1) / kTileM));
+  ozaki_form_kernel<<<grid, kThreads, smem, st>>>(
+      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, Y, ldy, err);
+  return cudaGetLastError();
+}
+
+}  // namespace spg

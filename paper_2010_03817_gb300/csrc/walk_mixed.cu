@@ -1,0 +1,850 @@
+// Mixed-precision path of the boundary oracle.  Per segment (line p + t v):
+//   V = sum v_j A_j arrives from the tensor-core formation (FP64 quality);
+//   F(p) is carried in FP64 from segment to segment (F <- F + t V).
+//   Stage 1 (FP32): Cholesky of F + sigma0 V and Lanczos on
+//     M = -L^{-1} V L^{-T} give an estimate t~ of t+ (Alg. 2) and u0.
+//   Stage 2 (FP64): Cholesky of F + sigma1 V with sigma1 just below t~ --
+//     the near-singular factorisation at the boundary stays in FP64 -- then a
+//     few power iterations on M_sigma1, whose dominant eigenvalue
+//     1/(t+ - sigma1) is separated by orders of magnitude, give t+ and the
+//     null vector u to FP64 accuracy.  Success of that factorisation
+//     certifies that F + sV > 0 on [0, sigma1], so the root found is the
+//     smallest positive one (Lemma "PEP and S cap C").
+//   Stage 3: normal w_j = u^T A_j u (Lemma "Gradient of det F") by a
+//     double-float (FP32 pair) contraction; reflection (Eq. "reflection").
+// t- (Hit-and-Run / intersection) comes from stage 1 refined by the FP64
+// pencil Rayleigh quotient -(u^T F u)/(u^T V u) with the exact F and V.
+#include <math.h>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "kernels.h"
+#include "lanczos.cuh"
+
+namespace spg {
+namespace {
+
+struct MixSmem {
+  uint8_t* R;     // region: stage 1 (G32, V32), stage 2 (G64), stage 3 (U hi, lo)
+  double* p;      // n
+  double* v;      // n
+  double* w;      // n + 1
+  double* wh;     // n
+  double* y;      // m
+  double* r;      // m
+  double* z;      // m
+  double* u;      // m
+  double* um;     // m (null vector at t-)
+  double* part;   // SPG_WARPS * m
+  double* scr;    // 320
+  double* bc;     // 16
+  float* q32;     // m
+  float* r32;     // m
+  float* z32;     // m
+  float* y32;     // m
+  float* ym32;    // m
+  float* col32;   // m
+  LanczosScalars* sc;
+  int* ib;        // 16
+};
+
+__device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global,
+                             size_t region_bytes) {
+  MixSmem s;
+  uint8_t* q = base;
+  if (region_global) {
+    s.R = region_global;
+  } else {
+    s.R = q;
+    q += (region_bytes + 15) & ~size_t(15);
+  }
+  double* d = reinterpret_cast<double*>(q);
+  s.p = d; d += n;
+  s.v = d; d += n;
+  s.w = d; d += n + 1;
+  s.wh = d; d += n;
+  s.y = d; d += m;
+  s.r = d; d += m;
+  s.z = d; d += m;
+  s.u = d; d += m;
+  s.um = d; d += m;
+  s.part = d; d += (size_t)SPG_WARPS * m;
+  s.scr = d; d += 320;
+  s.bc = d; d += 16;
+  float* f = reinterpret_cast<float*>(d);
+  s.q32 = f; f += m;
+  s.r32 = f; f += m;
+  s.z32 = f; f += m;
+  s.y32 = f; f += m;
+  s.ym32 = f; f += m;
+  s.col32 = f; f += m;  // 6 m floats: the next address stays 8-byte aligned
+  s.sc = reinterpret_cast<LanczosScalars*>(f);
+  s.ib = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(s.sc) + sizeof(LanczosScalars));
+  return s;
+}
+
+struct MixResult {
+  double t_plus, t_minus;
+  int status, iters, retries, fallback, power;
+  int learned;  // 1: warm start accepted, -1: rejected, 0: not used
+};
+
+// unit length, largest-magnitude entry positive (CTA-wide, FP64)
+__device__ void normalise_vec(double* u, int m, MixSmem& sm) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < m; i += SPG_THREADS) a += u[i] * u[i];
+  const double nrm = sqrt(block_sum(a, sm.sc->red));
+  if (threadIdx.x == 0) {
+    int big = 0;
+    for (int i = 1; i < m; ++i)
+      if (fabs(u[i]) > fabs(u[big])) big = i;
+    sm.bc[0] = (u[big] < 0.0 ? -1.0 : 1.0) / nrm;
+  }
+  __syncthreads();
+  const double sc = sm.bc[0];
+  for (int i = threadIdx.x; i < m; i += SPG_THREADS) u[i] *= sc;
+  __syncthreads();
+}
+
+// pencil Rayleigh quotient t = -(u^T F u)/(u^T V u) with F, V packed FP64
+__device__ double pencil_rq(const double* Fg, const double* Vg, const double* u, int m,
+                            MixSmem& sm) {
+  symv_packed<double>(Fg, u, sm.r, m, 1.0, sm.part);
+  symv_packed<double>(Vg, u, sm.z, m, 1.0, sm.part);
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < m; i += SPG_THREADS) {
+    a += u[i] * sm.r[i];
+    b += u[i] * sm.z[i];
+  }
+  a = block_sum(a, sm.sc->red);
+  b = block_sum(b, sm.sc->red);
+  return -a / b;
+}
+
+__device__ __forceinline__ void stage_mark(const MixWork& mw, int stage, long long& t0) {
+  if (mw.prof && threadIdx.x == 0) {
+    const long long t1 = clock64();
+    atomicAdd(reinterpret_cast<unsigned long long*>(&mw.prof[blockIdx.x * kProfSlots + stage]),
+              (unsigned long long)(t1 - t0));
+    t0 = t1;
+  }
+}
+
+// Stage 2 for one end of the chord: FP64 Cholesky of F + sigma1 V with
+// sigma1 = sigma0 + (t_est - sigma0)(1 - delta) just inside that end, power
+// iteration on M_sigma1 from u0 (in sm.u), FP64 Lanczos fallback.  On return
+// sm.u holds the unit null vector and *t the root.  plus: t+ end (else t-).
+// cold: no usable estimate (factor at sigma0 and go straight to Lanczos).
+__device__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+                               const double* __restrict__ Fg, const double* __restrict__ Vg,
+                               double* __restrict__ Q64, double sigma0, double t_est, bool cold,
+                               double* t, MixResult* res, bool plus = true) {
+  const int tid = threadIdx.x;
+  const int m = sp.m;
+  const long long P = sp.P;
+  double* G64 = reinterpret_cast<double*>(sm.R);
+  long long tmark = clock64();
+  double sigma1 = sigma0;
+  bool ok = false;
+  if (!cold) {
+    double delta = mw.delta1;
+    for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+      sigma1 = sigma0 + (t_est - sigma0) * (1.0 - delta);
+      for (long long e = tid; e < P; e += SPG_THREADS) G64[e] = Fg[e] + sigma1 * Vg[e];
+      if (tid == 0) sm.ib[0] = 0;
+      __syncthreads();
+      ok = factor_cholesky<double>(G64, m, sm.part, &sm.ib[0]);
+      if (!ok) {
+        ++res->retries;
+        delta *= 8.0;
+      }
+    }
+  }
+  const bool power = ok;
+  if (!ok) {
+    sigma1 = sigma0;
+    for (long long e = tid; e < P; e += SPG_THREADS) G64[e] = Fg[e] + sigma0 * Vg[e];
+    if (tid == 0) sm.ib[0] = 0;
+    __syncthreads();
+    ok = factor_cholesky<double>(G64, m, sm.part, &sm.ib[0]);
+    if (!ok) {
+      *t = 0.0;
+      return kNotPD;
+    }
+  }
+  stage_mark(mw, 2, tmark);  // FP64 fill + Cholesky
+  double mu = 0.0;
+  bool converged = false;
+  if (power) {
+    // y = L^T u0, then power iteration on M_sigma1: its dominant eigenvalue is
+    // 1/(t - sigma1) for the root t at this end.  A small deterministic
+    // perturbation of u0 gives every eigenvector a component, so that an
+    // estimate of the wrong root (two nearly equal roots) cannot pass the
+    // residual test by an absent component: it converges to the right root
+    // or fails over to the Lanczos solve.
+    {
+      double a = 0.0;
+      for (int i = tid; i < m; i += SPG_THREADS) a += sm.u[i] * sm.u[i];
+      const double nu = sqrt(block_sum(a, sm.sc->red));
+      for (int i = tid; i < m; i += SPG_THREADS)
+        sm.u[i] += 1e-4 * nu * sin(1.3 * i + 0.7) / sqrt((double)m);
+      __syncthreads();
+    }
+    mul_upper<double>(G64, sm.u, sm.y, m, sm.part);
+    invert_diag_blocks<double>(G64, m);
+    PencilOp<double> op{G64, Vg, true, sm.part};
+    for (int it = 0; it < mw.power_iters; ++it) {
+      double a = 0.0;
+      for (int i = tid; i < m; i += SPG_THREADS) a += sm.y[i] * sm.y[i];
+      const double ny = sqrt(block_sum(a, sm.sc->red));
+      for (int i = tid; i < m; i += SPG_THREADS) sm.y[i] /= ny;
+      __syncthreads();
+      apply_pencil<double>(op, sm.y, sm.r, sm.z, m, sm.scr);
+      double b = 0.0;
+      for (int i = tid; i < m; i += SPG_THREADS) b += sm.y[i] * sm.r[i];
+      mu = block_sum(b, sm.sc->red);
+      double c = 0.0;
+      for (int i = tid; i < m; i += SPG_THREADS) {
+        const double d = sm.r[i] - mu * sm.y[i];
+        c += d * d;
+      }
+      const double resid = sqrt(block_sum(c, sm.sc->red));
+      for (int i = tid; i < m; i += SPG_THREADS) sm.y[i] = sm.r[i];
+      __syncthreads();
+      ++res->power;
+      if (resid <= mw.tol64 * fabs(mu)) {
+        converged = true;
+        break;
+      }
+    }
+    // certificate: the dominant eigenvalue belongs to this end and its root
+    // lies closer to sigma1 than 0 does (then no root of the other side can
+    // dominate); sign: mu > 0 for t+, mu < 0 for t-
+    if (plus ? !(mu > 0.0 && 1.0 / mu < sigma1) : !(mu < 0.0 && -1.0 / mu < -sigma1))
+      converged = false;
+  } else {
+    invert_diag_blocks<double>(G64, m);
+  }
+  stage_mark(mw, 3, tmark);  // FP64 power iterations
+  if (!converged) {
+    res->fallback = 1;
+    // robust fallback: FP64 Lanczos for the extreme eigenvalue of this end
+    PencilOp<double> op{G64, Vg, true, sm.part};
+    for (int i = tid; i < m; i += SPG_THREADS) sm.z[i] = 1.0 + 0.5 * sin(0.7 * i + 0.1);
+    __syncthreads();
+    // (cold start on the t+ side: also the t- end, for the Hit-and-Run chord)
+    const bool both = !plus || cold;
+    LanczosOut lo = lanczos_extreme<double>(op, Q64, sm.z, sm.r, sm.u, sm.scr, sm.y,
+                                            plus ? sm.um : sm.y, m, mw.kmax64, both, mw.tol64,
+                                            sm.sc);
+    res->iters += lo.iters;
+    mu = plus ? lo.theta_max : lo.theta_min;
+    if (plus && cold) {
+      res->t_minus = lo.theta_min < 0.0 ? sigma1 + 1.0 / lo.theta_min : -INFINITY;
+      if (lo.theta_min < 0.0) {
+        solve_upper<double>(G64, sm.um, m, sm.scr);
+        normalise_vec(sm.um, m, sm);
+      }
+    }
+    converged = lo.converged;
+    if (plus ? !(mu > 0.0) : !(mu < 0.0)) {
+      *t = plus ? INFINITY : -INFINITY;
+      stage_mark(mw, 4, tmark);
+      return kUnbounded;
+    }
+  }
+  stage_mark(mw, 4, tmark);  // FP64 Lanczos fallback
+  *t = sigma1 + 1.0 / mu;
+  // u = L^{-T} y
+  for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = sm.y[i];
+  __syncthreads();
+  solve_upper<double>(G64, sm.u, m, sm.scr);
+  normalise_vec(sm.u, m, sm);
+  return converged ? kOk : kNoConv;
+}
+
+// One boundary-oracle evaluation in mixed precision (CTA-wide).
+//   Fg, Vg: packed FP64 F(p) and V (global).  sigma0: stage-1 shift.
+__device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+                                   const double* __restrict__ Fg, const double* __restrict__ Vg,
+                                   float* __restrict__ Q32, double* __restrict__ Q64,
+                                   double sigma0, bool want_min, bool stage2,
+                                   const float* __restrict__ pred = nullptr,
+                                   double t_scale = 0.0, double margin = 0.0) {
+  const int tid = threadIdx.x;
+  const int m = sp.m;
+  const long long P = sp.P;
+  MixResult res;
+  res.retries = 0;
+  res.iters = 0;
+  res.fallback = 0;
+  res.power = 0;
+  res.learned = 0;
+  res.t_minus = -INFINITY;
+  float* G32 = reinterpret_cast<float*>(sm.R);
+  float* V32 = G32 + P;
+  double* G64 = reinterpret_cast<double*>(sm.R);
+  long long tmark = clock64();
+
+  // ---------------- stage 1 (learned): shifted power iteration --------------
+  // The network predicts t+ and the null vector u.  Factor F + sigma0 V with
+  // sigma0 = (1 - margin) t^ and iterate on M_sigma0 from L^T u^: its
+  // dominant eigenvalue is 1/(t+ - sigma0).  Accepted when it converges and
+  // t+ - sigma0 < sigma0 (no root below sigma0 can dominate); otherwise the
+  // plain stage 1 below runs.
+  double t1 = 0.0, t1m = -INFINITY;
+  bool have_t1 = false;
+  if (pred && !want_min) {
+    const double that = t_scale * exp((double)pred[0]);
+    double sig = that * (1.0 - margin);
+    bool okl = false;
+    for (int attempt = 0; attempt < 2 && !okl && isfinite(sig) && sig > 0.0; ++attempt) {
+      for (long long e = tid; e < P; e += SPG_THREADS) {
+        const double g = Vg[e];
+        G32[e] = (float)(Fg[e] + sig * g);
+        V32[e] = (float)g;
+      }
+      if (tid == 0) sm.ib[0] = 0;
+      __syncthreads();
+      okl = factor_cholesky<float>(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
+      if (!okl) {
+        ++res.retries;
+        sig *= 0.5;
+      }
+    }
+    stage_mark(mw, 0, tmark);
+    if (okl) {
+      for (int i = tid; i < m; i += SPG_THREADS) sm.z32[i] = pred[1 + i];
+      __syncthreads();
+      mul_upper<float>(G32, sm.z32, sm.y32, m, reinterpret_cast<float*>(sm.part));
+      invert_diag_blocks<float>(G32, m);
+      PencilOp<float> op{G32, V32, true, reinterpret_cast<float*>(sm.part)};
+      float mu = 0.f;
+      bool conv = false;
+      for (int it = 0; it < mw.learned_iters; ++it) {
+        float a = 0.f;
+        for (int i = tid; i < m; i += SPG_THREADS) a += sm.y32[i] * sm.y32[i];
+        const float ny = sqrtf(block_sum(a, reinterpret_cast<float*>(sm.sc->red)));
+        for (int i = tid; i < m; i += SPG_THREADS) sm.y32[i] /= ny;
+        __syncthreads();
+        apply_pencil<float>(op, sm.y32, sm.r32, sm.q32, m, reinterpret_cast<float*>(sm.scr));
+        float b = 0.f;
+        for (int i = tid; i < m; i += SPG_THREADS) b += sm.y32[i] * sm.r32[i];
+        mu = block_sum(b, reinterpret_cast<float*>(sm.sc->red));
+        float c = 0.f;
+        for (int i = tid; i < m; i += SPG_THREADS) {
+          const float d = sm.r32[i] - mu * sm.y32[i];
+          c += d * d;
+        }
+        const float resid = sqrtf(block_sum(c, reinterpret_cast<float*>(sm.sc->red)));
+        for (int i = tid; i < m; i += SPG_THREADS) sm.y32[i] = sm.r32[i];
+        __syncthreads();
+        ++res.iters;
+        if (resid <= (float)mw.tol32 * fabsf(mu)) {
+          conv = true;
+          break;
+        }
+      }
+      if (conv && mu > 0.f && 1.0 / mu < sig) {
+        sigma0 = sig;
+        t1 = sig + 1.0 / mu;
+        have_t1 = true;
+        solve_upper<float>(G32, sm.y32, m, reinterpret_cast<float*>(sm.scr));
+        for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = (double)sm.y32[i];
+        __syncthreads();
+      }
+    }
+    res.learned = have_t1 ? 1 : -1;
+    stage_mark(mw, 1, tmark);
+  }
+
+  // ---------------- stage 1: FP32 estimate ---------------------------------
+  bool ok = have_t1;
+  for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const double g = Vg[e];
+      G32[e] = (float)(Fg[e] + sigma0 * g);
+      V32[e] = (float)g;
+    }
+    if (tid == 0) sm.ib[0] = 0;
+    __syncthreads();
+    ok = factor_cholesky<float>(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
+    if (!ok) {
+      ++res.retries;
+      sigma0 *= 0.2;  // back off toward the point itself
+    }
+  }
+  stage_mark(mw, 0, tmark);  // stage 1 fill + FP32 Cholesky
+  int fp64_fallback = !ok;
+  if (ok && !have_t1) {
+    invert_diag_blocks<float>(G32, m);
+    for (int i = tid; i < m; i += SPG_THREADS) sm.q32[i] = 1.0f + 0.5f * __sinf(0.7f * i + 0.1f);
+    __syncthreads();
+    PencilOp<float> op{G32, V32, true, reinterpret_cast<float*>(sm.part)};
+    LanczosOut lo = lanczos_extreme<float>(op, Q32, sm.q32, sm.r32, sm.z32,
+                                           reinterpret_cast<float*>(sm.scr), sm.y32, sm.ym32, m,
+                                           mw.kmax32, want_min, mw.tol32, sm.sc);
+    res.iters += lo.iters;
+    if (!(lo.theta_max > 0.0)) {
+      res.status = kUnbounded;
+      res.t_plus = INFINITY;
+      return res;
+    }
+    t1 = sigma0 + 1.0 / lo.theta_max;
+    // u0 = L^{-T} y (FP32), kept as the start vector of stage 2
+    solve_upper<float>(G32, sm.y32, m, reinterpret_cast<float*>(sm.scr));
+    if (want_min) {
+      if (lo.theta_min < 0.0) {
+        t1m = sigma0 + 1.0 / lo.theta_min;
+        solve_upper<float>(G32, sm.ym32, m, reinterpret_cast<float*>(sm.scr));
+        for (int i = tid; i < m; i += SPG_THREADS) sm.um[i] = (double)sm.ym32[i];
+        __syncthreads();
+      }
+    }
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = (double)sm.y32[i];
+    __syncthreads();
+  }
+  stage_mark(mw, 1, tmark);  // FP32 Lanczos
+  if (want_min && isfinite(t1m)) {
+    // t- from the FP64 pencil Rayleigh quotient (stationary at the eigenvector)
+    res.t_minus = pencil_rq(Fg, Vg, sm.um, m, sm);
+    normalise_vec(sm.um, m, sm);
+  }
+
+  if (!stage2 && !fp64_fallback) {
+    // t+ from the FP64 pencil Rayleigh quotient of the stage-1 vector
+    res.t_plus = pencil_rq(Fg, Vg, sm.u, m, sm);
+    normalise_vec(sm.u, m, sm);
+    res.status = kOk;
+    return res;
+  }
+  // ---------------- stage 2: FP64 factorisation next to the boundary -------
+  if (fp64_fallback) t1 = 0.0;
+  if (want_min && isfinite(t1m) && !fp64_fallback) {
+    // t- end: the same refinement on the negative side (u0 of t- is in um)
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = sm.um[i];
+    __syncthreads();
+    double tm;
+    int st = refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, t1m, false, &tm, &res, false);
+    if (st == kOk) {
+      res.t_minus = tm;
+      for (int i = tid; i < m; i += SPG_THREADS) sm.um[i] = sm.u[i];
+      __syncthreads();
+    }
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = (double)sm.y32[i];
+    __syncthreads();
+  }
+  double tp;
+  res.status = refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, fp64_fallback ? 0.0 : t1,
+                               fp64_fallback, &tp, &res);
+  res.t_plus = tp;
+  return res;
+}
+
+// w_j = u^T A_j u, j = 0..n, by a double-float contraction over the packed
+// entries: A_j = hi + lo (FP32 pair, precomputed), U = u_i u_k (x2 off the
+// diagonal) as an FP32 pair; each product is split exactly with an FMA and
+// the high parts are summed with TwoSum, the rounding errors of both kept in
+// a separate accumulator (Ogita, Rump, Oishi: Sum2 / Dot2).  Error ~ n eps^2
+// of sum |terms| (eps = 2^-24), returned as hi + lo in FP64.
+__device__ void contract_forms(const DevSpec& sp, const float2* __restrict__ Ahl, MixSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = sp.n, m = sp.m;
+  const long long P = sp.P;
+  float* Uh = reinterpret_cast<float*>(sm.R);
+  float* Ul = Uh + P;
+  // u as FP32 pairs
+  float* uh = sm.q32;
+  float* ul = sm.r32;
+  for (int i = tid; i < m; i += SPG_THREADS) {
+    const float h = (float)sm.u[i];
+    uh[i] = h;
+    ul[i] = (float)(sm.u[i] - (double)h);
+  }
+  __syncthreads();
+  for (long long e = tid; e < P; e += SPG_THREADS) {
+    const uint32_t ik = sp.pidx[e];
+    const int i = ik >> 16, k = ik & 0xffff;
+    const float a = uh[i], b = uh[k];
+    const float p = a * b;
+    float q = fmaf(a, b, -p);
+    q = fmaf(a, ul[k], fmaf(ul[i], b, q));
+    const float s = p + q;  // |q| << |p|: fast two-sum
+    const float t = q - (s - p);
+    const float f = (i == k) ? 1.0f : 2.0f;
+    Uh[e] = f * s;
+    Ul[e] = f * t;
+  }
+  __syncthreads();
+  for (int j = wid; j <= n; j += SPG_WARPS) {
+    const float2* Aj = Ahl + (size_t)j * P;
+    float acc = 0.f, lo = 0.f;
+    for (long long e = lane; e < P; e += 32) {
+      const float2 a = Aj[e];
+      const float uh_e = Uh[e], ul_e = Ul[e];
+      const float p = a.x * uh_e;
+      const float pe = fmaf(a.x, uh_e, -p);
+      // TwoSum(acc, p)
+      const float s = acc + p;
+      const float bb = s - acc;
+      const float err = (acc - (s - bb)) + (p - bb);
+      acc = s;
+      lo += err + fmaf(a.x, ul_e, fmaf(a.y, uh_e, pe));
+    }
+    double tot = (double)acc + (double)lo;
+    tot = warp_sum(tot);
+    if (lane == 0) sm.w[j] = tot;
+  }
+  __syncthreads();
+}
+
+__device__ double mix_unit_normal(MixSmem& sm, int n) {
+  double a = 0.0;
+  for (int j = threadIdx.x; j < n; j += SPG_THREADS) a += sm.w[j + 1] * sm.w[j + 1];
+  const double nw = sqrt(block_sum(a, sm.sc->red));
+  if (nw > 0.0)
+    for (int j = threadIdx.x; j < n; j += SPG_THREADS) sm.wh[j] = sm.w[j + 1] / nw;
+  __syncthreads();
+  return nw;
+}
+
+__device__ void draw_direction(uint64_t seed, uint32_t chain, uint32_t step, double* v, int n,
+                               MixSmem& sm) {
+  for (int i = threadIdx.x; 2 * i < n; i += SPG_THREADS) {
+    double g0, g1;
+    rng_gauss_pair(seed, chain, step, (uint32_t)i, &g0, &g1);
+    v[2 * i] = g0;
+    if (2 * i + 1 < n) v[2 * i + 1] = g1;
+  }
+  __syncthreads();
+  double a = 0.0;
+  for (int j = threadIdx.x; j < n; j += SPG_THREADS) a += v[j] * v[j];
+  const double nv = sqrt(block_sum(a, sm.sc->red));
+  for (int j = threadIdx.x; j < n; j += SPG_THREADS) v[j] /= nv;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// walk: one segment per active chain per launch (wave)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SPG_THREADS, 1)
+    mixed_wave_kernel(DevSpec sp, MixWork mw, MixWave wv) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n, m = sp.m;
+  const long long P = sp.P;
+  const size_t cta = blockIdx.x;
+  uint8_t* rg = mw.region_global ? mw.region_global + cta * mw.region_bytes : nullptr;
+  MixSmem sm = mix_carve(smem_raw, n, m, rg, mw.region_bytes);
+  float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
+  double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
+  const int count = *wv.count_cur;
+  for (int r = blockIdx.x; r < count; r += gridDim.x) {
+    const int c = wv.id_cur[r];
+    const uint32_t chain = wv.chain0 + (uint32_t)c;
+    double* Fc = wv.F + (size_t)c * P;
+    const double* Vr = wv.Vrows + (size_t)r * P;
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      sm.p[j] = wv.X[(size_t)c * n + j];
+      sm.v[j] = wv.dir_cur[(size_t)r * n + j];
+    }
+    double ell = wv.ell[c];
+    int nrefl = wv.nrefl[c];
+    const double tprev = wv.tprev[c];
+    long long* st = wv.stats + (size_t)c * kNumStats;
+    __syncthreads();
+    const double sigma0 = (wv.kind == 0 && nrefl > 0) ? mw.sigma_frac * tprev : 0.0;
+    const float* prow =
+        (wv.pred && wv.kind == 0) ? wv.pred + (size_t)r * wv.ld_pred : nullptr;
+    MixResult res = segment_mixed(sp, mw, sm, Fc, Vr, Q32, Q64, sigma0, wv.kind != 0,
+                                  wv.kind == 0, prow, wv.t_scale, wv.margin);
+    if (wv.rec_x && wv.kind == 0 && res.status == kOk && isfinite(res.t_plus)) {
+      // training tuple: (x * x_scale, v) -> (log(t+ / t_scale), u)
+      if (tid == 0) sm.ib[2] = atomicAdd(wv.rec_count, 1);
+      __syncthreads();
+      const int slot = sm.ib[2];
+      if (slot < wv.rec_cap) {
+        float* fx = wv.rec_x + (size_t)slot * 2 * n;
+        float* fy = wv.rec_y + (size_t)slot * (1 + m);
+        for (int j = tid; j < n; j += SPG_THREADS) {
+          fx[j] = (float)(sm.p[j] * wv.x_scale);
+          fx[n + j] = (float)sm.v[j];
+        }
+        for (int i = tid; i < m; i += SPG_THREADS) fy[1 + i] = (float)sm.u[i];
+        if (tid == 0) fy[0] = (float)log(res.t_plus / wv.t_scale);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      st[kStatSegments] += 1;
+      st[kStatLanczos] += res.iters;
+      st[kStatShiftRetry] += res.retries;
+      st[kStatFallback] += res.fallback;
+      st[kStatPower] += res.power;
+      if (res.learned > 0) st[kStatLearnedOk] += 1;
+      if (res.learned < 0) st[kStatLearnedMiss] += 1;
+      if (res.status == kNoConv) st[kStatNoConv] += 1;
+    }
+    if (res.status == kNoConv) res.status = kOk;
+    int status = res.status;
+    bool step_done = false, rejected = false;
+    double move = 0.0;
+    if (wv.kind == 0) {
+      if (status == kOk && res.t_plus < ell) {
+        long long tc0 = clock64();
+        contract_forms(sp, mw.Ahl, sm);
+        stage_mark(mw, 5, tc0);  // normal contraction
+        const double nw = mix_unit_normal(sm, n);
+        if (!(nw > 0.0)) {
+          status = kDegenerate;
+        } else {
+          double a = 0.0;
+          for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.wh[j];
+          const double vw = block_sum(a, sm.sc->red);
+          move = (1.0 - wv.kappa) * res.t_plus;
+          for (int j = tid; j < n; j += SPG_THREADS) {
+            sm.p[j] += move * sm.v[j];
+            sm.v[j] -= 2.0 * vw * sm.wh[j];
+          }
+          ell -= res.t_plus;
+          ++nrefl;
+          if (tid == 0) st[kStatReflections] += 1;
+          if (nrefl > wv.rho) {
+            status = kRho;
+          }
+        }
+      } else if (status == kOk) {
+        move = ell;
+        for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += ell * sm.v[j];
+        step_done = true;
+      }
+    } else {
+      if (status == kOk && !(isfinite(res.t_plus) && isfinite(res.t_minus))) status = kUnbounded;
+      if (status == kOk) {
+        const double eta = rng_uniform(wv.seed, chain, wv.step0 + wv.done[c], kStreamEta);
+        move = res.t_minus + eta * (res.t_plus - res.t_minus);
+        for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += move * sm.v[j];
+        step_done = true;
+      }
+    }
+    __syncthreads();
+    long long tu0 = clock64();
+    if (status != kOk) {
+      // the step is rejected: back to its start point; F(x) is re-formed
+      rejected = true;
+      step_done = true;
+      for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] = wv.Xstart[(size_t)c * n + j];
+      __syncthreads();
+      for (long long e = tid; e < P; e += SPG_THREADS) {
+        const double* Ae = sp.A + e;
+        double f = Ae[0];
+        for (int j = 0; j < n; ++j) f += sm.p[j] * Ae[(size_t)(j + 1) * P];
+        Fc[e] = f;
+      }
+      if (tid == 0) {
+        st[kStatBadSteps] += 1;
+        wv.status[c] = status;
+      }
+    } else if (move != 0.0) {
+      // carried F: F(p + move v) = F(p) + move V
+      for (long long e = tid; e < P; e += SPG_THREADS) Fc[e] += move * Vr[e];
+    }
+    __syncthreads();
+    int done = wv.done[c];
+    if (step_done) {
+      ++done;
+      nrefl = 0;
+      ell = 0.0;
+      for (int j = tid; j < n; j += SPG_THREADS) wv.Xstart[(size_t)c * n + j] = sm.p[j];
+      if (done < wv.steps) {
+        const uint32_t stp = wv.step0 + (uint32_t)done;
+        if (wv.kind == 2) {
+          const double uc = rng_uniform(wv.seed, chain, stp, kStreamCoord);
+          int jc = (int)(uc * n);
+          jc = jc < n ? jc : n - 1;
+          for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = (j == jc) ? 1.0 : 0.0;
+          __syncthreads();
+        } else {
+          draw_direction(wv.seed, chain, stp, sm.v, n, sm);
+        }
+        if (wv.kind == 0) ell = -wv.tau * log(rng_uniform(wv.seed, chain, stp, kStreamEta));
+      }
+    }
+    for (int j = tid; j < n; j += SPG_THREADS) wv.X[(size_t)c * n + j] = sm.p[j];
+    if (done < wv.steps) {
+      // still active: queue the chain (and its direction) for the next wave
+      if (tid == 0) sm.ib[1] = atomicAdd(wv.count_next, 1);
+      __syncthreads();
+      const int slot = sm.ib[1];
+      for (int j = tid; j < n; j += SPG_THREADS) wv.dir_next[(size_t)slot * n + j] = sm.v[j];
+      if (tid == 0) wv.id_next[slot] = c;
+    }
+    stage_mark(mw, 6, tu0);  // F update, next direction, queueing
+    if (tid == 0) {
+      wv.done[c] = done;
+      wv.ell[c] = ell;
+      wv.nrefl[c] = nrefl;
+      wv.tprev[c] = (rejected || step_done) ? 0.0 : res.t_plus;
+    }
+    __syncthreads();
+  }
+}
+
+// first wave of a walk call: directions and lengths of the first step
+__global__ void mixed_begin_kernel(DevSpec sp, MixWave wv) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int n = sp.n;
+  MixSmem sm;
+  double* d = reinterpret_cast<double*>(smem_raw);
+  sm.v = d;
+  sm.sc = reinterpret_cast<LanczosScalars*>(d + n + 1);
+  for (int c = blockIdx.x; c < wv.C; c += gridDim.x) {
+    const uint32_t chain = wv.chain0 + (uint32_t)c;
+    if (wv.kind == 2) {
+      const double uc = rng_uniform(wv.seed, chain, wv.step0, kStreamCoord);
+      int jc = (int)(uc * n);
+      jc = jc < n ? jc : n - 1;
+      for (int j = threadIdx.x; j < n; j += SPG_THREADS) sm.v[j] = (j == jc) ? 1.0 : 0.0;
+      __syncthreads();
+    } else {
+      draw_direction(wv.seed, chain, wv.step0, sm.v, n, sm);
+    }
+    for (int j = threadIdx.x; j < n; j += SPG_THREADS) {
+      wv.dir_cur[(size_t)c * n + j] = sm.v[j];
+      wv.Xstart[(size_t)c * n + j] = wv.X[(size_t)c * n + j];
+    }
+    if (threadIdx.x == 0) {
+      wv.id_cur[c] = c;
+      wv.done[c] = 0;
+      wv.nrefl[c] = 0;
+      wv.tprev[c] = 0.0;
+      wv.ell[c] = wv.kind == 0
+                      ? -wv.tau * log(rng_uniform(wv.seed, chain, wv.step0, kStreamEta))
+                      : 0.0;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *wv.count_cur = wv.C;
+}
+
+// ---------------------------------------------------------------------------
+// primitives (intersection / reflection) in mixed precision
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SPG_THREADS, 1)
+    prim_mixed_kernel(DevSpec sp, MixWork mw, PrimParams pp, const double* Frows,
+                      const double* Vrows) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n, m = sp.m;
+  const long long P = sp.P;
+  const size_t cta = blockIdx.x;
+  uint8_t* rg = mw.region_global ? mw.region_global + cta * mw.region_bytes : nullptr;
+  MixSmem sm = mix_carve(smem_raw, n, m, rg, mw.region_bytes);
+  float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
+  double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
+  for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
+    for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = pp.v[(size_t)c * n + j];
+    __syncthreads();
+    MixResult res = segment_mixed(sp, mw, sm, Frows + (size_t)c * P, Vrows + (size_t)c * P, Q32,
+                                  Q64, 0.0, pp.op == 0, true);
+    int status = res.status == kNoConv ? kOk : res.status;
+    if (pp.op == 0) {
+      if (tid == 0) {
+        pp.t_plus[c] = res.t_plus;
+        pp.t_minus[c] = res.t_minus;
+        pp.status[c] = res.status;
+      }
+      if (pp.u && status == kOk)
+        for (int i = tid; i < m; i += SPG_THREADS) pp.u[(size_t)c * m + i] = sm.u[i];
+    } else {
+      if (status == kOk) {
+        contract_forms(sp, mw.Ahl, sm);
+        const double nw = mix_unit_normal(sm, n);
+        if (!(nw > 0.0)) status = kDegenerate;
+      }
+      if (status == kOk) {
+        double a = 0.0;
+        for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.wh[j];
+        const double vw = block_sum(a, sm.sc->red);
+        for (int j = tid; j < n; j += SPG_THREADS) {
+          pp.w_hat[(size_t)c * n + j] = sm.wh[j];
+          pp.s[(size_t)c * n + j] = sm.v[j] - 2.0 * vw * sm.wh[j];
+        }
+      }
+      if (tid == 0) {
+        pp.t_plus[c] = res.t_plus;
+        pp.status[c] = status == kOk ? res.status : status;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// features of the listed chains for the warm-start network: (x * x_scale, v)
+__global__ void learned_features_kernel(const double* __restrict__ X,
+                                        const double* __restrict__ dir, const int* __restrict__ id,
+                                        int count, int n, double x_scale,
+                                        float* __restrict__ feats) {
+  const long long total = (long long)count * n;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n), j = (int)(q % n);
+    feats[(size_t)r * 2 * n + j] = (float)(X[(size_t)id[r] * n + j] * x_scale);
+    feats[(size_t)r * 2 * n + n + j] = (float)dir[(size_t)r * n + j];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_learned_features(const double* X, const double* dir, const int* id, int count,
+                                    int n, double x_scale, float* feats, cudaStream_t st) {
+  const long long total = (long long)count * n;
+  long long g = (total + 255) / 256;
+  learned_features_kernel<<<(int)(g < 4096 ? (g > 0 ? g : 1) : 4096), 256, 0, st>>>(
+      X, dir, id, count, n, x_scale, feats);
+  return cudaGetLastError();
+}
+
+size_t mixed_region_bytes(int m) {
+  const size_t P = (size_t)m * (m + 1) / 2;
+  return P * 8;  // max of 2 P floats (stages 1, 3) and P doubles (stage 2)
+}
+
+size_t mixed_smem_bytes(int n, int m, bool region_in_smem) {
+  size_t b = region_in_smem ? ((mixed_region_bytes(m) + 15) & ~size_t(15)) : 0;
+  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 320 + 16);
+  b += 4 * (size_t)6 * m;
+  b += sizeof(LanczosScalars) + 16 * sizeof(int);
+  return b;
+}
+
+cudaError_t launch_mixed_wave(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
+                              cudaStream_t st) {
+  const size_t smem = mixed_smem_bytes(sp.n, sp.m, mw.region_global == nullptr);
+  cudaError_t e = cudaFuncSetAttribute(mixed_wave_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  mixed_wave_kernel<<<mw.ctas, SPG_THREADS, smem, st>>>(sp, mw, wv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_begin(const DevSpec& sp, const MixWave& wv, cudaStream_t st) {
+  const size_t smem = 8 * ((size_t)sp.n + 1) + sizeof(LanczosScalars);
+  const int grid = wv.C < 1024 ? wv.C : 1024;
+  mixed_begin_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_mixed(const DevSpec& sp, const MixWork& mw, const PrimParams& pp,
+                              const double* Frows, const double* Vrows, cudaStream_t st) {
+  const size_t smem = mixed_smem_bytes(sp.n, sp.m, mw.region_global == nullptr);
+  cudaError_t e = cudaFuncSetAttribute(prim_mixed_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = pp.count < mw.ctas ? pp.count : mw.ctas;
+  if (grid <= 0) return cudaSuccess;
+  prim_mixed_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, mw, pp, Frows, Vrows);
+  return cudaGetLastError();
+}
+
+}  // namespace spg

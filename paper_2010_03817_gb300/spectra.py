@@ -18,11 +18,11 @@ LIB_PATH = os.path.join(_HERE, "libspectra_gb.so")
 
 OK, EINVAL, ENOTPD, EUNBOUNDED, ENOCONV, ECUDA, ENOMEM = range(7)
 ST_OK, ST_NOT_PD, ST_UNBOUNDED, ST_NOCONV, ST_RHO, ST_DEGENERATE = range(6)
-MODE_FP64 = 0
-MODES = {"fp64": MODE_FP64}
+MODE_FP64, MODE_MIXED, MODE_LEARNED = 0, 1, 2
+MODES = {"fp64": MODE_FP64, "mixed": MODE_MIXED, "learned": MODE_LEARNED}
 STAT_NAMES = ["segments", "reflections", "bad_steps", "lanczos_iters", "shift_retries",
-              "noconv"]
-NUM_STATS = 8
+              "noconv", "fp64_fallbacks", "power_iters", "learned_ok", "learned_miss"]
+NUM_STATS = 12
 
 _lib = None
 _lock = threading.Lock()
@@ -61,6 +61,19 @@ def _bind(L):
     f("sp_set_state", [_vp, _vp, ctypes.c_uint32, _vp])
     f("sp_chain_status", [_vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp])
     f("sp_intersect_noalloc", [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp])
+    f("sp_form_pencil", [_vp, _i, _vp, _vp, _vp, _vp, _i, _vp])
+    f("sp_set_stage_timers", [_vp, _vp])
+    f("sp_attach_mlp", [_vp, _vp, _d, _d, _d, _i])
+    f("sp_record_tuples", [_vp, _vp, _vp, _i, _vp])
+    f("sp_kernel_timing", [_vp, _i, _vp])
+    f("sp_mlp_create", [_i, _i, _i, ctypes.c_uint64, ctypes.POINTER(_vp)])
+    f("sp_mlp_destroy", [_vp])
+    f("sp_mlp_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                      ctypes.POINTER(ctypes.c_longlong)])
+    f("sp_mlp_params", [_vp, _vp, _vp])
+    f("sp_mlp_forward", [_vp, _i, _vp, _vp, _vp])
+    f("sp_mlp_gradients", [_vp, _i, _vp, _vp, _vp, _vp, _vp])
+    f("sp_mlp_train", [_vp, _i, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp])
 
 
 def lib():
@@ -155,10 +168,39 @@ class Spectrahedron:
         except Exception:
             pass
 
+    def attach_mlp(self, net, x_scale: float = 1.0, t_scale: float = 1.0, margin: float = 0.05,
+                   iters: int = 12):
+        """Warm-start network for SP_MODE_LEARNED walks (None detaches)."""
+        self._mlp = net
+        _check(lib().sp_attach_mlp(self._h, net.handle if net is not None else None, x_scale,
+                                   t_scale, margin, iters))
+
+    def set_stage_timers(self, timers=None):
+        """Mixed-path stage timers: an int64 CUDA tensor (SMs x 8), or None."""
+        import torch
+        _check(lib().sp_set_stage_timers(self._h, _dev(timers, torch.int64) if timers is not None
+                                         else None))
+
     def set_solver(self, kmax: int = 96, tol: float = 1e-13, sigma_frac: float = 0.1):
         _check(lib().sp_set_solver(self._h, kmax, tol, sigma_frac))
 
     # -- primitives ---------------------------------------------------------
+    def form_pencil(self, x=None, v=None, mode: str = "fp64", stream=None):
+        """(F(x_c), V_c) as packed lower triangles (count x m(m+1)/2); either
+        argument may be None."""
+        import torch
+        ref = x if x is not None else v
+        C = ref.shape[0]
+        P = self.m * (self.m + 1) // 2
+        F = torch.empty((C, P), dtype=torch.float64, device=ref.device) if x is not None else None
+        V = torch.empty((C, P), dtype=torch.float64, device=ref.device) if v is not None else None
+        _check(lib().sp_form_pencil(
+            self._h, C, _dev(x, torch.float64, (C, self.n), "x") if x is not None else None,
+            _dev(v, torch.float64, (C, self.n), "v") if v is not None else None,
+            _dev(F) if F is not None else None, _dev(V) if V is not None else None, MODES[mode],
+            _stream(stream)))
+        return F, V
+
     def membership(self, x, stream=None):
         import torch
         C = x.shape[0]
@@ -268,6 +310,26 @@ class Chains:
             ptr = x.ctypes.data_as(_vp)
         _check(lib().sp_set_state(self._h, ptr, step, _stream(stream)))
 
+    def kernel_timing(self, enable: int = -1):
+        """Per-kernel CUDA-event timing of walk calls (see sp_kernel_timing)."""
+        out = (ctypes.c_double * 9)()
+        _check(lib().sp_kernel_timing(self._h, enable, out))
+        k = ["fp64_ms", "fp64_launches", "form_ms", "form_launches", "wave_ms", "wave_launches",
+             "mlp_ms", "mlp_launches", "other_launches"]
+        return {name: out[i] for i, name in enumerate(k)}
+
+    def record(self, x_out=None, y_out=None, count=None):
+        """Record (features, targets) tuples of later mixed / learned Billiard
+        walks into CUDA tensors (x_out: cap x 2n, y_out: cap x (1+m) float32,
+        count: int32 scalar tensor, zeroed by the caller); no arguments stop."""
+        import torch
+        if x_out is None:
+            _check(lib().sp_record_tuples(self._h, None, None, 0, None))
+            return
+        cap = x_out.shape[0]
+        _check(lib().sp_record_tuples(self._h, _dev(x_out, torch.float32), _dev(y_out, torch.float32),
+                                      cap, _dev(count, torch.int32)))
+
     def status(self, stream=None):
         """(per-chain status tensor, dict of summed statistics)."""
         import torch
@@ -275,3 +337,84 @@ class Chains:
         stats = (ctypes.c_longlong * NUM_STATS)()
         _check(lib().sp_chain_status(self._h, _dev(st), stats, _stream(stream)))
         return st, {k: int(stats[i]) for i, k in enumerate(STAT_NAMES)}
+
+
+class MLP:
+    """The warm-start network din -> dh -> dh -> dout on the GPU (sp_mlp_*)."""
+
+    def __init__(self, din: int, dh: int, dout: int, seed: int = 0):
+        h = _vp()
+        _check(lib().sp_mlp_create(din, dh, dout, seed, ctypes.byref(h)))
+        self._h = h
+        self.din, self.dh, self.dout = din, dh, dout
+        npar = ctypes.c_longlong(0)
+        _check(lib().sp_mlp_dims(h, None, None, None, ctypes.byref(npar)))
+        self.nparams = npar.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sp_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """[(name, shape)] of the flat parameter vector."""
+        doutp = (self.dout + 15) // 16 * 16
+        dinp = (self.din + 7) // 8 * 8
+        return [("W1", (self.dh, dinp)), ("b1", (self.dh,)), ("W2", (self.dh, self.dh)),
+                ("b2", (self.dh,)), ("W3", (doutp, self.dh)), ("b3", (doutp,))]
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().sp_mlp_params(self._h, out.ctypes.data_as(_vp), None))
+        return out
+
+    def set_params(self, flat) -> None:
+        flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        assert flat.size == self.nparams
+        _check(lib().sp_mlp_params(self._h, None, flat.ctypes.data_as(_vp)))
+
+    def unflatten(self, flat):
+        out, o = [], 0
+        for _, shp in self.layout():
+            k = int(np.prod(shp))
+            out.append(np.asarray(flat[o:o + k]).reshape(shp))
+            o += k
+        return out
+
+    def forward(self, X, stream=None):
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, self.dout), dtype=torch.float32, device=X.device)
+        _check(lib().sp_mlp_forward(self._h, B, _dev(X, torch.float32, (B, self.din), "X"),
+                                    _dev(Y), _stream(stream)))
+        return Y
+
+    def gradients(self, X, T, stream=None):
+        """(loss, flat gradient) for one batch (B a multiple of 8)."""
+        import torch
+        B = X.shape[0]
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().sp_mlp_gradients(self._h, B, _dev(X, torch.float32, (B, self.din), "X"),
+                                      _dev(T, torch.float32, (B, self.dout), "T"),
+                                      g.ctypes.data_as(_vp), ctypes.byref(loss), _stream(stream)))
+        return float(loss.value), g
+
+    def train(self, X, T, epochs: int, batch: int, lr: float, stream=None):
+        import torch
+        B = X.shape[0]
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(lib().sp_mlp_train(self._h, B, _dev(X, torch.float32, (B, self.din), "X"),
+                                  _dev(T, torch.float32, (B, self.dout), "T"), epochs, batch,
+                                  ctypes.c_float(lr), losses.ctypes.data_as(_vp), _stream(stream)))
+        return losses

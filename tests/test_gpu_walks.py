@@ -59,7 +59,7 @@ def test_cube_marginals(spectra, kind):
         getattr(ch, kind)(40)
     X = ch.state()[0].cpu().numpy()
     st, stats = ch.status()
-    assert stats["bad_steps"] == 0
+    assert stats["bad_steps"] == 0, (stats, np.unique(st.cpu().numpy(), return_counts=True))
     se_mean = math.sqrt(1.0 / 3.0 / C)
     se_var = math.sqrt((1.0 / 5.0 - 1.0 / 9.0) / C)
     assert np.all(np.abs(X.mean(0)) < 4.5 * se_mean)
