@@ -237,7 +237,7 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
     timers = None
     if stage_timers and mode != "fp64":
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        timers = torch.zeros((sms, 8), dtype=torch.int64, device="cuda")
+        timers = torch.zeros((sms, 16), dtype=torch.int64, device="cuda")
         spec.set_stage_timers(timers)
     chains.kernel_timing(1)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -259,10 +259,16 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
     if timers is not None:
         spec.set_stage_timers(None)
         tot = timers.sum(0).double()
-        names = ["fill+fp32_cholesky", "fp32_stage1_iterations", "fp64_fill+cholesky",
-                 "fp64_power", "fp64_fallback", "normal_contraction", "bookkeeping"]
-        share = {nm: float(tot[i] / tot.sum()) for i, nm in enumerate(names)}
-        share["cycles_per_segment"] = float(tot.sum()) / max(1, stats["segments"])
+        names = ["stage1_fill+fp32_cholesky", "stage1_fp32_lanczos", "stage2_fill+factorisation",
+                 "stage2_iterations", "fp64_lanczos_fallback", "normal_contraction",
+                 "bookkeeping"]
+        stages = tot[:7]
+        share = {nm: float(stages[i] / stages.sum()) for i, nm in enumerate(names)}
+        share["cycles_per_segment"] = float(stages.sum()) / max(1, stats["segments"])
+        lz = tot[8:12]
+        if float(lz.sum()) > 0:
+            share["lanczos_split"] = {nm: float(lz[i] / lz.sum()) for i, nm in
+                                      enumerate(["apply", "reorth", "check", "final"])}
     return dict(chains=chains, dev_ms=dev_ms, wall=wall, stats=stats, kt=kt, share=share,
                 steps=steps)
 

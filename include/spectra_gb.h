@@ -55,7 +55,7 @@ extern "C" {
 #define SP_MODE_FP64 0   /* every step in FP64 */
 #define SP_MODE_MIXED 1  /* tensor-core V formation (exact digit splitting, FP64 quality),
                             FP32 estimate, FP64 factorisation next to the boundary and FP64
-                            refinement of t+ and u; needs n + 1 <= 224 */
+                            refinement of t+ and u; needs n <= 224 */
 #define SP_MODE_LEARNED 2  /* the mixed path with the network's warm start (sp_attach_mlp)
                               for the Billiard walk; primitives run as SP_MODE_MIXED */
 
@@ -279,11 +279,14 @@ int sp_kernel_timing(sp_chains* ch, int enable, double* out);
 
 /*
  * Stage timers of the mixed path (profiling aid).  timers: device int64
- * array of (number of SMs) x 8 entries, zeroed by the caller, or NULL to
+ * array of (number of SMs) x 16 entries, zeroed by the caller, or NULL to
  * switch the timers off.  Block b adds the clock64() cycles it spends in
- * each stage of each segment to timers[8 b + k]: k = 0 stage-1 fill and FP32
- * Cholesky, 1 FP32 Lanczos, 2 FP64 fill and Cholesky, 3 FP64 power
- * iterations, 4 FP64 Lanczos fallback, 5 normal contraction, 6 bookkeeping.
+ * each stage of each segment to timers[16 b + k]: k = 0 stage-1 fill and
+ * FP32 Cholesky, 1 FP32 Lanczos, 2 stage-2 fill and factorisation (double-
+ * float, or FP64 on the fallback), 3 stage-2 power iterations, 4 FP64
+ * Lanczos fallback, 5 normal contraction, 6 bookkeeping; and inside every
+ * Lanczos run: 8 operator application, 9 reorthogonalisation, 10
+ * convergence checks, 11 final Ritz pairs.
  */
 int sp_set_stage_timers(sp_spec* s, long long* timers);
 

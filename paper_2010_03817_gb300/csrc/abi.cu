@@ -140,7 +140,7 @@ struct MixSpace {
     ctas = ctas_;
     rows = rows_;
     const size_t P = (size_t)m * (m + 1) / 2;
-    region_bytes = mixed_region_bytes(m);
+    region_bytes = mixed_region_bytes(n, m);
     const bool in_smem = mixed_smem_bytes(n, m, true) <= (size_t)max_smem_optin();
     bool ok = cudaMalloc(&Q32, sizeof(float) * (size_t)kmax32 * m * ctas) == cudaSuccess &&
               cudaMalloc(&Q64, sizeof(double) * (size_t)kmax64 * m * ctas) == cudaSuccess &&
@@ -321,8 +321,8 @@ int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_sp
     delete s;
     return cuda_fail(e1 != cudaSuccess ? e1 : e2, "sp_create_spectrahedron: upload");
   }
-  // mixed path: BF16 digits of the stack (n + 1 <= kOzakiMaxK) and FP32 pairs
-  if (n + 1 <= kOzakiMaxK && !(flags & 1u)) {
+  // mixed path: BF16 digits of A_1..A_n (n <= kOzakiMaxK) and FP32 pairs
+  if (n <= kOzakiMaxK && !(flags & 1u)) {
     const size_t nb = ozaki_b_bytes(P, n);
     std::vector<uint16_t> bsl(nb / 2);
     std::vector<int> ecol(P);
@@ -390,7 +390,7 @@ static int check_mode(int mode, const char* fn) {
 
 static int check_mixed(const sp_spec* s, const char* fn) {
   if (!s->mixed_ok)
-    return fail(SP_EINVAL, "%s: the mixed path needs n + 1 <= 224 (tensor-core formation)", fn);
+    return fail(SP_EINVAL, "%s: the mixed path needs n <= 224 (tensor-core formation)", fn);
   return SP_OK;
 }
 
@@ -398,12 +398,12 @@ static int check_mixed(const sp_spec* s, const char* fn) {
 static int form_rows_mixed(sp_spec* s, MixSpace& ms, int count, const double* x,
                            const double* v, double* F_out, double* V_out, cudaStream_t st) {
   if (x && F_out) {
-    cudaError_t e = launch_ozaki_form(x, count, s->n, 1.0, s->Bsl, s->ecol, s->P, ms.digits,
+    cudaError_t e = launch_ozaki_form(x, count, s->n, 1.0, s->A, s->Bsl, s->ecol, s->P, ms.digits,
                                       ms.erow, F_out, s->P, ms.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (F)");
   }
   if (v && V_out) {
-    cudaError_t e = launch_ozaki_form(v, count, s->n, 0.0, s->Bsl, s->ecol, s->P, ms.digits,
+    cudaError_t e = launch_ozaki_form(v, count, s->n, 0.0, s->A, s->Bsl, s->ecol, s->P, ms.digits,
                                       ms.erow, V_out, s->P, ms.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (V)");
   }
@@ -690,7 +690,7 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
   cudaStream_t st = (cudaStream_t)stream;
   const DevSpec ds = s->dev();
   if (!ch->F_valid) {
-    cudaError_t e = launch_ozaki_form(ch->X, ch->C, s->n, 1.0, s->Bsl, s->ecol, s->P,
+    cudaError_t e = launch_ozaki_form(ch->X, ch->C, s->n, 1.0, s->A, s->Bsl, s->ecol, s->P,
                                       ch->ms.digits, ch->ms.erow, ch->F, s->P, ch->ms.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (F)");
     ch->F_valid = true;
@@ -750,7 +750,7 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
     e = cudaMemsetAsync(wv.count_next, 0, sizeof(int), st);
     if (ch->timing) cudaEventRecord(ev[0], st);
     if (e == cudaSuccess)
-      e = launch_ozaki_form(wv.dir_cur, count, s->n, 0.0, s->Bsl, s->ecol, s->P, ch->ms.digits,
+      e = launch_ozaki_form(wv.dir_cur, count, s->n, 0.0, s->A, s->Bsl, s->ecol, s->P, ch->ms.digits,
                             ch->ms.erow, ch->ms.Vrows, s->P, ch->ms.err, st);
     if (ch->timing) cudaEventRecord(ev[1], st);
     ch->n_form += 2;  // digit slicing + tensor-core formation

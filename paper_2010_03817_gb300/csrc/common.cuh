@@ -74,6 +74,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// broadcast from lane src (overloaded for the double-float type)
+__device__ __forceinline__ float shfl_idx(float v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ double shfl_idx(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll

@@ -7,6 +7,8 @@
 // the inverses of the corresponding blocks of L; the off-diagonal blocks hold
 // L.  The triangular solves use exactly that layout.
 #pragma once
+#include <string.h>
+
 #include "common.cuh"
 
 namespace spg {
@@ -32,76 +34,146 @@ __device__ __forceinline__ double recip_t(double x) {
 }
 
 // In-place Cholesky G = L L^T of the packed lower triangle G (m x m),
-// right-looking in panels of kPanel columns: the panel is factored column by
-// column, then the trailing matrix receives one rank-kPanel update (kPanel
-// FMAs per load and store of G).
-// pan: scratch of kPanel * m elements (the panel, transposed).
-// Returns true on success (CTA-uniform); on failure *flag = 1 + the first
-// column whose pivot was not positive.
-constexpr int kPanel = 4;
+// right-looking in panels of kPanel = 8 columns, three barriers per panel:
+//   1. warp 0 factors the 8 x 8 diagonal block in registers (lane r holds
+//      row r of the block; column c is broadcast by shuffles);
+//   2. every row below solves against it (one thread per row, forward
+//      substitution with the block read as broadcasts from shared memory) and
+//      leaves its 8 entries in the transposed panel copy pan[c][i];
+//   3. the trailing lower triangle receives the rank-8 update in 4 x 4
+//      register tiles (8 + 8 panel loads per 128 FMAs).
+// pan: scratch of cholesky_scratch(m) elements.  Returns true on success
+// (CTA-uniform); on failure *flag = 1 + the first column whose pivot was not
+// positive (or outside the range where the FP32-seeded reciprocal square root
+// holds).
+constexpr int kPanel = 8;
+__host__ __device__ inline int chol_ld(int m) { return (m + 6) & ~3; }
+__host__ __device__ inline size_t cholesky_scratch(int m) {
+  return (size_t)kPanel * chol_ld(m) + 4;
+}
+
+// four consecutive elements from 16-byte aligned shared memory (vector loads)
 template <typename T>
-__device__ bool factor_cholesky(T* G, int m, T* pan, int* flag) {
-  const int tid = threadIdx.x;
+__device__ __forceinline__ void load4(const T* p, T (&v)[4]) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    const float f[4] = {q.x, q.y, q.z, q.w};
+    memcpy(v, f, sizeof(f));
+  } else {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    memcpy(v, f, sizeof(f));
+  }
+}
+
+template <typename T>
+__device__ bool factor_cholesky(T* G, int m, T* pan_raw, int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // 16-byte aligned panel base; row stride ld (a multiple of 4, >= m + 3)
+  T* pan = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(pan_raw) + 15) & ~uintptr_t(15));
+  const int ld = chol_ld(m);
   for (int jb = 0; jb < m; jb += kPanel) {
     const int nb = min(kPanel, m - jb);
-    // ---- panel: columns jb .. jb+nb-1 -------------------------------------
-    for (int c = 0; c < nb; ++c) {
-      const int j = jb + c;
-      if (tid == 0) {
-        const T dj = G[tri(j, j)];
-        // the FP32 seed of rsqrt_t needs dj inside the FP32 range
-        if (!(dj > T(1e-37)) || !(dj < T(3e37))) {
-          *flag = j + 1;
-        } else {
-          const T r = rsqrt_t(dj);  // 1/l
-          G[tri(j, j)] = dj * r;    // l = sqrt(dj)
-          pan[c * m + j] = r;
-        }
-      }
-      __syncthreads();
-      if (*flag) return false;
-      const T rl = pan[c * m + j];
-      for (int i = j + 1 + tid; i < m; i += SPG_THREADS) {
-        const T v = G[tri(i, j)] * rl;
-        G[tri(i, j)] = v;
-        pan[c * m + i] = v;
-      }
-      __syncthreads();
-      // remaining panel columns: G[i][jb+c2] -= L[i][j] L[jb+c2][j], i >= jb + c2
-      const int rest = nb - 1 - c;
-      if (rest > 0) {
-        const int rows = m - (j + 1);
-        for (int q = tid; q < rows * rest; q += SPG_THREADS) {
-          const int i = j + 1 + q / rest;
-          const int c2 = c + 1 + q % rest;
-          const int k = jb + c2;
-          if (i >= k) G[tri(i, k)] -= pan[c * m + i] * pan[c * m + k];
-        }
-        __syncthreads();
-      }
-    }
-    // ---- trailing update, rows / columns >= j0: rank-nb --------------------
     const int j0 = jb + nb;
-    const int s = m - j0;
-    if (s <= 0) break;
-    const int total = s * (s + 1) / 2;
-    if (tid < total) {
-      int i = j0, off = tid;  // element (i, j0 + off)
-      while (off > i - j0) {
-        off -= i - j0 + 1;
-        ++i;
+    // ---- 1. diagonal block ---------------------------------------------------
+    if (wid == 0) {
+      T row[kPanel];
+      const bool mine = lane < nb;
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c)
+        row[c] = (mine && c <= lane) ? G[tri(jb + lane, jb + c)] : T(0);
+      int bad = 0;
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        if (c < nb && !bad) {
+          const T d = shfl_idx(row[c], c);
+          if (!(d > T(1e-37)) || !(d < T(3e37))) {
+            bad = c + 1;
+          } else {
+            const T rinv = rsqrt_t(d);
+            if (lane == c) row[c] = d * rinv;
+            if (lane > c) row[c] *= rinv;
+#pragma unroll
+            for (int c2 = c + 1; c2 < kPanel; ++c2) {
+              const T l2 = shfl_idx(row[c], c2);
+              if (c2 <= lane) row[c2] -= row[c] * l2;
+            }
+            if (lane == 0) pan[c * ld + jb + c] = rinv;  // 1 / L_cc for step 2
+          }
+        }
       }
-      for (int q = tid; q < total; q += SPG_THREADS) {
-        const int k = j0 + off;
-        T acc = G[tri(i, k)];
+      if (bad) {
+        if (lane == 0) *flag = jb + bad;
+      } else if (mine) {
 #pragma unroll
         for (int c = 0; c < kPanel; ++c)
-          if (c < nb) acc -= pan[c * m + i] * pan[c * m + k];
-        G[tri(i, k)] = acc;
-        off += SPG_THREADS;
-        while (i < m && off > i - j0) {
-          off -= i - j0 + 1;
-          ++i;
+          if (c <= lane) {
+            G[tri(jb + lane, jb + c)] = row[c];
+            if (c < lane) pan[c * ld + jb + lane] = row[c];  // L_bb[lane][c]
+          }
+      }
+    }
+    __syncthreads();
+    if (*flag) return false;
+    if (j0 >= m) break;
+    // ---- 2. panel rows below the block ----------------------------------------
+    for (int i = j0 + tid; i < m; i += SPG_THREADS) {
+      const size_t base = tri(i, jb);
+      T g[kPanel];
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) g[c] = G[base + c];
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        T acc = g[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) acc -= g[k] * pan[k * ld + jb + c];
+        g[c] = acc * pan[c * ld + jb + c];
+      }
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        G[base + c] = g[c];
+        pan[c * ld + i] = g[c];
+      }
+    }
+    // rows m .. ld-1 of the copy read as zeros by the edge tiles
+    for (int q = tid; q < kPanel * (ld - m); q += SPG_THREADS)
+      pan[(q / (ld - m)) * ld + m + q % (ld - m)] = T(0);
+    __syncthreads();
+    // ---- 3. trailing update, 4 x 4 tiles of the lower triangle ---------------
+    const int s = m - j0;
+    const int nt = (s + 3) >> 2;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int t = tid; t < ntiles; t += SPG_THREADS) {
+      int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while (I * (I + 1) / 2 > t) --I;
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      const int K = t - I * (I + 1) / 2;
+      const int i0 = j0 + 4 * I, k0 = j0 + 4 * K;
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        T va[4], vb[4];
+        load4<T>(pan + c * ld + i0, va);
+        load4<T>(pan + c * ld + k0, vb);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += va[a] * vb[b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = i0 + a;
+        if (i < m) {
+          T* gi = G + tri(i, 0);
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (k0 + b <= i) gi[k0 + b] -= acc[a][b];
         }
       }
     }
@@ -147,21 +219,45 @@ __device__ void solve_lower(const T* L, T* x, int m, T* s) {
   for (int b = 0; b < nb; ++b) {
     const int r0 = b * kBlk;
     const int bs = min(kBlk, m - r0);
-    // s_r = x_r - sum_{k < r0} L[r][k] x_k
-    for (int rr = wid; rr < bs; rr += SPG_WARPS) {
-      const int r = r0 + rr;
-      const T* row = L + tri(r, 0);
-      T acc = T(0);
-      for (int k = lane; k < r0; k += 32) acc += row[k] * x[k];
-      acc = warp_sum(acc);
-      if (lane == 0) s[rr] = x[r] - acc;
+    // s_r = x_r - sum_{k < r0} L[r][k] x_k; warp w takes the rows w + 8 q of
+    // the block, their dot products interleaved
+    {
+      constexpr int kRows = kBlk / SPG_WARPS;
+      T acc[kRows];
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) acc[q] = T(0);
+      for (int k = lane; k < r0; k += 32) {
+        const T xk = x[k];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+          const int rr = wid + SPG_WARPS * q;
+          if (rr < bs) acc[q] += L[tri(r0 + rr, k)] * xk;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+          const int rr = wid + SPG_WARPS * q;
+          if (rr < bs) s[rr] = x[r0 + rr] - acc[q];
+        }
+      }
     }
     __syncthreads();
     if (wid == 0 && lane < bs) {
+      // four independent partial sums (the chain of FMAs is the latency)
       const T* row = L + tri(r0 + lane, r0);
-      T acc = T(0);
-      for (int c = 0; c <= lane; ++c) acc += row[c] * s[c];
-      x[r0 + lane] = acc;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int c = 0;
+      for (; c + 3 <= lane; c += 4) {
+        a0 += row[c] * s[c];
+        a1 += row[c + 1] * s[c + 1];
+        a2 += row[c + 2] * s[c + 2];
+        a3 += row[c + 3] * s[c + 3];
+      }
+      for (; c <= lane; ++c) a0 += row[c] * s[c];
+      x[r0 + lane] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
   }
@@ -179,10 +275,16 @@ __device__ void solve_upper(const T* L, T* x, int m, T* s) {
     const int bs = min(kBlk, m - r0);
     const int i = r0 + lane;
     // partial sums of sum_{r >= r0+bs} L[r][i] x_r, rows split over warps
-    T acc = T(0);
-    if (lane < bs)
-      for (int r = r0 + bs + wid; r < m; r += SPG_WARPS) acc += L[tri(r, i)] * x[r];
-    part[wid * kBlk + lane] = acc;
+    T acc = T(0), acc2 = T(0);
+    if (lane < bs) {
+      int r = r0 + bs + wid;
+      for (; r + SPG_WARPS < m; r += 2 * SPG_WARPS) {
+        acc += L[tri(r, i)] * x[r];
+        acc2 += L[tri(r + SPG_WARPS, i)] * x[r + SPG_WARPS];
+      }
+      if (r < m) acc += L[tri(r, i)] * x[r];
+    }
+    part[wid * kBlk + lane] = acc + acc2;
     __syncthreads();
     if (wid == 0 && lane < bs) {
       T t = x[i];
@@ -192,10 +294,17 @@ __device__ void solve_upper(const T* L, T* x, int m, T* s) {
     }
     __syncthreads();
     if (wid == 0 && lane < bs) {
-      // z_i = sum_{r >= i in block} Dinv[r][i] s_r
-      T z = T(0);
-      for (int rr = lane; rr < bs; ++rr) z += L[tri(r0 + rr, i)] * s[rr];
-      x[i] = z;
+      // z_i = sum_{r >= i in block} Dinv[r][i] s_r, four partial sums
+      T z0 = T(0), z1 = T(0), z2 = T(0), z3 = T(0);
+      int rr = lane;
+      for (; rr + 3 < bs; rr += 4) {
+        z0 += L[tri(r0 + rr, i)] * s[rr];
+        z1 += L[tri(r0 + rr + 1, i)] * s[rr + 1];
+        z2 += L[tri(r0 + rr + 2, i)] * s[rr + 2];
+        z3 += L[tri(r0 + rr + 3, i)] * s[rr + 3];
+      }
+      for (; rr < bs; ++rr) z0 += L[tri(r0 + rr, i)] * s[rr];
+      x[i] = (z0 + z1) + (z2 + z3);
     }
     __syncthreads();
   }
@@ -226,21 +335,21 @@ __device__ void gemv_full(const T* __restrict__ A, const T* x, T* y, int m, T al
 // second kind of contribution in per-lane registers (m <= 32 * kMaxColBlocks).
 // part: scratch of SPG_WARPS * m elements.
 constexpr int kMaxColBlocks = 16;
-template <typename T>
-__device__ void symv_packed(const T* __restrict__ V, const T* z, T* y, int m, T alpha, T* part) {
+template <typename T, typename S = T>
+__device__ void symv_packed(const S* __restrict__ V, const T* z, T* y, int m, T alpha, T* part) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   T cacc[kMaxColBlocks];
 #pragma unroll
   for (int i = 0; i < kMaxColBlocks; ++i) cacc[i] = T(0);
   for (int r = wid; r < m; r += SPG_WARPS) {
-    const T* row = V + tri(r, 0);
+    const S* row = V + tri(r, 0);
     const T zr = z[r];
     T acc = T(0);
 #pragma unroll
     for (int i = 0; i < kMaxColBlocks; ++i) {
       const int k = lane + 32 * i;
       if (k <= r) {
-        const T a = row[k];
+        const T a = T(row[k]);
         acc += a * z[k];
         if (k < r) cacc[i] += a * zr;
       }

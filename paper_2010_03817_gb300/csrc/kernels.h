@@ -96,7 +96,7 @@ struct MixWork {
   int ctas;
   long long* prof;  // optional: per-CTA clock64 sums per stage (kProfSlots each)
 };
-constexpr int kProfSlots = 8;
+constexpr int kProfSlots = 16;  // 0-6: stages, 8-11: Lanczos sub-stages
 
 struct MixWave {
   int kind, C, steps, rho;
@@ -131,7 +131,7 @@ struct MixWave {
   double x_scale;
 };
 
-size_t mixed_region_bytes(int m);
+size_t mixed_region_bytes(int n, int m);
 cudaError_t launch_learned_features(const double* X, const double* dir, const int* id, int count,
                                     int n, double x_scale, float* feats, cudaStream_t st);
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem);
@@ -149,10 +149,10 @@ int ozaki_kp(int n);
 size_t ozaki_b_bytes(long long P, int n);
 size_t ozaki_row_bytes(int R, int n);
 void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol);
-cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const uint16_t* Bsl,
-                              const int* ecol, long long P, void* row_digits, int* erow,
-                              double* Y, long long ldy, int* err, cudaStream_t st);
-constexpr int kOzakiMaxK = 224;  // n + 1 limit of the tensor-core formation
+cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const double* A0,
+                              const uint16_t* Bsl, const int* ecol, long long P, void* row_digits,
+                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st);
+constexpr int kOzakiMaxK = 224;  // n limit of the tensor-core formation
 
 // BF16 GEMM on tcgen05: C = A B^T (+ bias) (ReLU); FP32 and / or BF16 output
 cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,

@@ -32,8 +32,18 @@ struct LanczosScalars {
   float b2f[kMaxLanczos + 1];
   float sf[2 * kMaxLanczos];     // FP32 Ritz coefficients + Thomas scratch
   double theta_max, theta_min, res_max, res_min;
+  long long* prof;               // optional clock64 sums per sub-stage (4 slots) or null
   int K, done, flag, precise;
 };
+
+// add the cycles since t0 to sub-stage slot s of the profile (thread 0)
+__device__ __forceinline__ void lz_mark(LanczosScalars* sc, int s, long long& t0) {
+  if (sc->prof && threadIdx.x == 0) {
+    const long long t1 = clock64();
+    atomicAdd(reinterpret_cast<unsigned long long*>(sc->prof + s), (unsigned long long)(t1 - t0));
+    t0 = t1;
+  }
+}
 
 // Sturm count: number of eigenvalues of T below x
 __device__ __forceinline__ int sturm_count(const double* a, const double* b, int K, double x) {
@@ -208,6 +218,39 @@ __device__ inline double tri_eigpair64(const double* a, const double* b, int K, 
   return tri_eigvec<double>(a, b, K, rq, s, cw);
 }
 
+// warp 0 (all lanes): the extreme eigenpair of T_K (largest if want_max, else
+// smallest) to FP64 accuracy.  Inverse iteration converges to the eigenvalue
+// nearest to its shift, which for a shift from an FP32 analysis need not be
+// the extreme one when two eigenvalues lie within the FP32 resolution of the
+// spectrum; an FP64 Sturm count certifies that no eigenvalue lies beyond the
+// result, else an FP64 multisection finds the extreme eigenvalue and the
+// inverse iteration restarts there.  s, cw: K-vectors (s receives the
+// normalised eigenvector).
+__device__ inline double tri_extreme_pair64(const double* a, const double* b, int K, double est,
+                                            bool want_max, double* s, double* cw) {
+  const int lane = threadIdx.x & 31;
+  double th = 0.0;
+  int beyond = 0;
+  if (lane == 0) {
+    th = tri_eigpair64(a, b, K, est, s, cw);
+    double nt = 0.0;
+    for (int i = 0; i < K; ++i)
+      nt = fmax(nt, fabs(a[i]) + (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < K ? fabs(b[i + 1]) : 0.0));
+    const double d = 1e-13 * fabs(th) + 8.0 * K * 2.2e-16 * nt;
+    beyond = !isfinite(th) ||
+             (want_max ? sturm_count(a, b, K, th + d) < K : sturm_count(a, b, K, th - d) > 0);
+  }
+  beyond = __shfl_sync(0xffffffffu, beyond, 0);
+  th = __shfl_sync(0xffffffffu, th, 0);
+  if (beyond) {
+    const double xe = tri_extreme(a, b, K, want_max);
+    if (lane == 0) th = tri_eigpair64(a, b, K, xe, s, cw);
+    th = __shfl_sync(0xffffffffu, th, 0);
+  }
+  __syncwarp();
+  return th;
+}
+
 // FP32 inverse iteration on the FP32 copies (a, b): same scheme as tri_eigvec
 __device__ inline float tri_eigvec_f(const float* a, const float* b, int K, float theta, float* s,
                                      float* cw) {
@@ -289,7 +332,8 @@ struct LanczosOut {
 template <typename T>
 __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, T* q, T* r, T* z,
                                       T* s, T* ymax, T* ymin, int m, int kmax, bool want_min,
-                                      double tol, LanczosScalars* sc) {
+                                      double tol, LanczosScalars* sc, int check_from = 6,
+                                      int check_every = 4) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   kmax = min(min(kmax, kMaxLanczos), m);
   // normalise q
@@ -308,10 +352,12 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
     __syncthreads();
   }
   int K = 0;
+  long long tz = clock64();
   for (int k = 0; k < kmax; ++k) {
     T* Qk = Q + (size_t)k * m;
     for (int i = tid; i < m; i += SPG_THREADS) Qk[i] = q[i];
     apply_pencil(op, q, r, z, m, s);
+    lz_mark(sc, 0, tz);
     // two passes of classical Gram-Schmidt against Q[0..k]; the coefficients
     // are kept in T (a double -> float conversion runs on the FP64 pipe)
     T* hT = reinterpret_cast<T*>(sc->h);
@@ -361,23 +407,28 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
       sc->b2f[K] = (float)(beta * beta);
     }
     __syncthreads();
+    lz_mark(sc, 1, tz);
     // convergence test every few steps (and on breakdown / last step)
     const bool breakdown = !(beta > 1e-300) ||
                            beta <= 1e-15 * fabs(alpha) + 1e-300;
-    const bool check = breakdown || K == kmax || (K >= 6 && (K % 4 == 0));
+    const bool check =
+        breakdown || K == kmax || (K >= check_from && ((K - check_from) % check_every == 0));
     if (check) {
       if (wid == 0) {
-        // FP32 analysis first; the FP64 inverse iteration only once the FP32
-        // residual estimate has reached its floor (or for the final answer)
+        // FP32 analysis first; the FP64 analysis (certified extreme eigenpair
+        // of T_K) only once the FP32 residual estimate has reached its floor
+        // (or on breakdown / at the last step)
         const float tmaxf = tri_extreme_f(sc->af, sc->b2f, K, true);
         const float tminf = want_min ? tri_extreme_f(sc->af, sc->b2f, K, false) : 0.f;
+        const double eps_t = sizeof(T) == 8 ? 2.2e-16 : 1.2e-7;
+        int ok = 0, precise = 0;
+        float thf = 0.f, thnf = 0.f;
         if (lane == 0) {
-          const double eps_t = sizeof(T) == 8 ? 2.2e-16 : 1.2e-7;
           float* sfv = sc->sf;
           float* cwf = sc->sf + kMaxLanczos;
-          const float thf = tri_eigvec_f(sc->af, sc->bf, K, tmaxf, sfv, cwf);
+          thf = tri_eigvec_f(sc->af, sc->bf, K, tmaxf, sfv, cwf);
           const float rmf = fabsf((float)beta * sfv[K - 1]);
-          float thnf = 0.f, rnf = 0.f;
+          float rnf = 0.f;
           if (want_min) {
             thnf = tri_eigvec_f(sc->af, sc->bf, K, tminf, sfv, cwf);
             rnf = fabsf((float)beta * sfv[K - 1]);
@@ -387,21 +438,24 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
           const float floorT = (float)(64.0 * eps_t) * bigf;
           bool ok32 = rmf <= fmaxf((float)tol * fabsf(thf), floorT);
           if (want_min) ok32 = ok32 && rnf <= fmaxf((float)tol * fabsf(thnf), floorT);
-          bool at_floor = rmf <= 4.f * floor32 && (!want_min || rnf <= 4.f * floor32);
-          bool ok = false;
-          if (sizeof(T) == 4 || (double)tol >= 1e-6) {
+          const bool at_floor = rmf <= 4.f * floor32 && (!want_min || rnf <= 4.f * floor32);
+          if (sizeof(T) == 4 || (double)tol >= 1e-6)
             ok = ok32;
-          } else if (at_floor || breakdown || K == kmax) {
-            // FP64 residual estimate: inverse iteration at the FP32 estimate
+          else
+            precise = at_floor || breakdown || K == kmax;
+        }
+        precise = __shfl_sync(0xffffffffu, precise, 0);
+        if (precise) {
+          const double th = tri_extreme_pair64(sc->alpha, sc->beta, K, (double)tmaxf, true,
+                                               sc->s_max, sc->cwork);
+          double thn = 0.0;
+          if (want_min)
+            thn = tri_extreme_pair64(sc->alpha, sc->beta, K, (double)tminf, false, sc->s_min,
+                                     sc->cwork);
+          if (lane == 0) {
             sc->precise = 1;
-            double th = tri_eigpair64(sc->alpha, sc->beta, K, (double)thf, sc->s_max,
-                                            sc->cwork);
             const double rm = fabs(beta * sc->s_max[K - 1]);
-            double thn = 0.0, rn = 0.0;
-            if (want_min) {
-              thn = tri_eigpair64(sc->alpha, sc->beta, K, (double)thnf, sc->s_min, sc->cwork);
-              rn = fabs(beta * sc->s_min[K - 1]);
-            }
+            const double rn = want_min ? fabs(beta * sc->s_min[K - 1]) : 0.0;
             const double big = fmax(fabs(th), fabs(thn));
             const double floor_ = 64.0 * eps_t * big;
             ok = rm <= fmax(tol * fabs(th), floor_);
@@ -409,7 +463,9 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
             sc->theta_max = th;
             sc->theta_min = thn;
           }
-          if (!sc->precise) {
+        }
+        if (lane == 0) {
+          if (!precise) {
             sc->theta_max = thf;
             sc->theta_min = thnf;
           }
@@ -417,6 +473,7 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
         }
       }
       __syncthreads();
+      lz_mark(sc, 2, tz);
       if (sc->done) break;
     }
     {
@@ -427,11 +484,18 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
   }
   // final Ritz pairs: FP64 inverse iteration at the last estimate (also the
   // FP64 Rayleigh quotient of T_K)
-  if (tid == 0) {
-    sc->theta_max = tri_eigpair64(sc->alpha, sc->beta, K, sc->theta_max, sc->s_max, sc->cwork);
+  if (wid == 0) {
+    const double th = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_max, true, sc->s_max,
+                                         sc->cwork);
+    double thn = 0.0;
     if (want_min)
-      sc->theta_min = tri_eigpair64(sc->alpha, sc->beta, K, sc->theta_min, sc->s_min, sc->cwork);
-    sc->K = K;
+      thn = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_min, false, sc->s_min,
+                               sc->cwork);
+    if (lane == 0) {
+      sc->theta_max = th;
+      if (want_min) sc->theta_min = thn;
+      sc->K = K;
+    }
   }
   __syncthreads();
   for (int i = tid; i < m; i += SPG_THREADS) {
@@ -445,6 +509,7 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
     if (want_min) ymin[i] = (T)b;
   }
   __syncthreads();
+  lz_mark(sc, 3, tz);
   LanczosOut o;
   o.theta_max = sc->theta_max;
   o.theta_min = want_min ? sc->theta_min : 0.0;

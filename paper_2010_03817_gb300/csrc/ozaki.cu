@@ -1,23 +1,28 @@
 // FP64-quality formation of the pencil matrices on the BF16 tensor cores.
 //
-// For R coefficient rows c_r (length n+1) the kernel computes
-//   Y[r, p] = sum_j c_r[j] A[j, p]            (A: packed LMI stack, (n+1) x P)
-// i.e. V = sum v_j A_j (rows c = (0, v)) and F(x) = A_0 + sum x_j A_j (rows
-// c = (1, x)) -- the pencil B_0 + t B_1 of a line (Lemma "PEP and S cap C").
+// For R coefficient rows c_r (length n) the kernel computes
+//   Y[r, p] = lead A_0[p] + sum_{j>=1} c_r[j] A[j, p]   (A: packed LMI stack)
+// i.e. V = sum v_j A_j (lead 0) and F(x) = A_0 + sum x_j A_j (lead 1) -- the
+// pencil B_0 + t B_1 of a line (Lemma "PEP and S cap C").  A_0 stays out of
+// the digit split (its entries are often much larger than those of A_1..A_n,
+// and the split's error scales with the largest entry of its operand): it is
+// added in FP64 by the epilogue.
 //
 // Exactness scheme (error-free splitting of both operands into integer
 // digits, the Ozaki scheme; Ozaki, Ogita, Oishi, Rump 2012, and its
 // tensor-core form, Mukunoki, Ozaki, Ogita, Imamura 2020):
 //   c_r[j] = 2^{f_r} sum_s a_s[r, j] 2^{-7(s+1)},  A[j, p] = 2^{e_p} sum_t b_t[j, p] 2^{-7(t+1)}
+// (j = 1..n)
 // with integer digits |a_s|, |b_t| <= 64 (exact in BF16), S = 7 digits (49
 // bits).  For each digit-sum d = s + t <= 6 the tensor core accumulates
 //   G_d[r, p] = sum_{s+t=d} sum_j a_s[r, j] b_t[j, p]
-// in FP32 in TMEM; every partial sum is an integer below 7 * 208 * 2^12 < 2^24,
+// in FP32 in TMEM; every partial sum is an integer below 7 * 224 * 2^12 < 2^24,
 // so the accumulation is exact.  The epilogue combines the seven integers in
 // 64-bit integer arithmetic and scales once into FP64:
 //   Y = 2^{f_r + e_p} sum_d G_d 2^{-7(d+2)}.
 // The truncation (pairs with s + t > 6, digits beyond the 7th) is below
-// (n+1) 2^-44 max_j |c_r[j]| max_j |A[j, p]|.
+// n 2^-44 max_j |c_r[j]| max_{j>=1} |A[j, p]|, plus one FP64 rounding of the
+// sum with lead A_0[p].
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -39,14 +44,45 @@ __device__ __forceinline__ uint32_t core_off(int r, int g, int kgroups) {
   return (uint32_t)(((r >> 3) * kgroups + g) * 128 + (r & 7) * 16);
 }
 
-// one warp per row: exponent and digits of c_r = (lead, vec[r, 0..n-1])
-__global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, double lead,
-                                  int Kp, __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
+// T 2^scale rounded to the nearest double (ties to even) with integer
+// operations only; |T| < 2^126, and the result stays in the normal range for
+// the exponents of LMI entries and coefficients.
+__device__ __forceinline__ double i128_to_double(__int128 T, int scale) {
+  if (T == 0) return 0.0;
+  const unsigned long long sign = T < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned __int128 a = T < 0 ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
+  int nbits = ah ? 128 - __clzll((long long)ah) : 64 - __clzll((long long)al);
+  unsigned long long mant;
+  const int sh = nbits - 53;
+  if (sh <= 0) {
+    mant = (unsigned long long)a << (-sh);
+  } else {
+    const unsigned __int128 q = a >> sh;
+    const unsigned __int128 rem = a - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    mant = (unsigned long long)q;
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++nbits;
+      }
+    }
+  }
+  const long long ex = (long long)(nbits - 1 + scale) + 1023;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) |
+                                          (mant & 0xfffffffffffffull)));
+}
+
+// one warp per row: exponent and digits of c_r = vec[r, 0..n-1]
+__global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, int Kp,
+                                  __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= R) return;
   const double* row = vec + (size_t)r * n;
-  double mx = fabs(lead);
+  double mx = 0.0;
   for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(row[j]));
   mx = warp_max(mx);
   int e = 0;
@@ -56,12 +92,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, 
   }
   if (lane == 0) ex[r] = e;
   for (int k = lane; k < Kp; k += 32) {
-    double y = 0.0;
-    if (k == 0)
-      y = lead;
-    else if (k <= n)
-      y = row[k - 1];
-    y = ldexp(y, -e);
+    double y = k < n ? ldexp(row[k], -e) : 0.0;
 #pragma unroll
     for (int s = 0; s < kDigits; ++s) {
       y *= 128.0;
@@ -75,7 +106,8 @@ __global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, 
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_form_kernel(const __nv_bfloat16* __restrict__ Asl, const int* __restrict__ erow, int R,
                       const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ ecol,
-                      long long P, int Kp, double* __restrict__ Y, long long ldy, int* err) {
+                      long long P, int Kp, const double* __restrict__ A0, double lead,
+                      double* __restrict__ Y, long long ldy, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int kgroups = Kp / 8;
@@ -172,7 +204,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const long long g = (long long)__float2ll_rn(__uint_as_float(v[i]));
+          // exact integers below 2^24 in magnitude
+          const long long g = (long long)__float2int_rn(__uint_as_float(v[i]));
           if (d <= 3)
             hi[i] = hi[i] * (1ll << kDigitBits) + g;
           else
@@ -185,10 +218,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 16; ++i) {
           const long long p = p0 + c0 + i;
           if (p < P) {
-            const int e = er + ecol[p];
-            // hi carries digit sums d = 0..3 (weight 2^{-7(d+2)} = 2^{7(3-d) - 35}),
-            // lo carries d = 4..6 (2^{7(6-d) - 56})
-            yrow[p] = ldexp((double)hi[i], e - 35) + ldexp((double)lo[i], e - 56);
+            // hi carries digit sums d = 0..3, lo d = 4..6:
+            //   Y = 2^(e - 56) (hi 2^21 + lo), one rounding (integer ops)
+            const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
+                                            er + ecol[p] - 56);
+            yrow[p] = lead != 0.0 ? fma(lead, A0[p], y) : y;
           }
         }
       }
@@ -201,19 +235,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-size_t ozaki_b_bytes(long long P, int n) {
-  const int Kp = ((n + 1) + 15) / 16 * 16;
-  return (size_t)kDigits * (size_t)P * Kp * 2;
-}
+int ozaki_kp(int n) { return (n + 15) / 16 * 16; }
 
-int ozaki_kp(int n) { return ((n + 1) + 15) / 16 * 16; }
+size_t ozaki_b_bytes(long long P, int n) { return (size_t)kDigits * (size_t)P * ozaki_kp(n) * 2; }
 
-// host: digits of the A stack, column by column (packed entry p over j = 0..n)
+// host: digits of A_1..A_n, column by column (packed entry p over j = 1..n)
 void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol) {
   const int Kp = ozaki_kp(n);
   for (long long p = 0; p < P; ++p) {
     double mx = 0.0;
-    for (int j = 0; j <= n; ++j) mx = fmax(mx, fabs(packed[(size_t)j * P + p]));
+    for (int j = 1; j <= n; ++j) mx = fmax(mx, fabs(packed[(size_t)j * P + p]));
     int e = 0;
     if (mx > 0.0) {
       frexp(mx, &e);
@@ -221,7 +252,7 @@ void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, 
     }
     ecol[p] = e;
     for (int k = 0; k < Kp; ++k) {
-      double y = (k <= n) ? ldexp(packed[(size_t)k * P + p], -e) : 0.0;
+      double y = (k < n) ? ldexp(packed[(size_t)(k + 1) * P + p], -e) : 0.0;
       for (int s = 0; s < kDigits; ++s) {
         y *= 128.0;
         const double d = rint(y);
@@ -238,13 +269,13 @@ void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, 
 
 size_t ozaki_row_bytes(int R, int n) { return (size_t)kDigits * R * ozaki_kp(n) * 2; }
 
-cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const uint16_t* Bsl,
-                              const int* ecol, long long P, void* row_digits, int* erow,
-                              double* Y, long long ldy, int* err, cudaStream_t st) {
+cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const double* A0,
+                              const uint16_t* Bsl, const int* ecol, long long P, void* row_digits,
+                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   const int Kp = ozaki_kp(n);
   __nv_bfloat16* Asl = static_cast<__nv_bfloat16*>(row_digits);
-  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, lead, Kp, Asl, erow);
+  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, Kp, Asl, erow);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)kDigits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
@@ -253,7 +284,8 @@ cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, cons
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((P + kTileN - 1) / kTileN), (unsigned)((R + kTileM - 1) / kTileM));
   ozaki_form_kernel<<<grid, kThreads, smem, st>>>(
-      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, Y, ldy, err);
+      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, A0, lead, Y, ldy,
+      err);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ struct Smem {
   double* ymax;  // m
   double* ymin;  // m
   double* u;     // m
-  double* col;   // kPanel * m (Cholesky panel)
+  double* col;   // cholesky_scratch(m) (Cholesky panel)
   double* scr;   // 288 + 32
   LanczosScalars* sc;
   double* bc;    // small broadcast area (16 doubles)
@@ -65,10 +65,11 @@ __device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
   s.ymax = q; q += m;
   s.ymin = q; q += m;
   s.u = q; q += m;
-  s.col = q; q += (size_t)kPanel * m;
+  s.col = q; q += cholesky_scratch(m);
   s.scr = q; q += 320;
   s.bc = q; q += 16;
   s.sc = reinterpret_cast<LanczosScalars*>(q);
+  if (threadIdx.x == 0) s.sc->prof = nullptr;
   q += (sizeof(LanczosScalars) + 7) / 8;
   s.ib = reinterpret_cast<int*>(q);
   return s;
@@ -454,7 +455,8 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
 
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem) {
   const size_t P = (size_t)m * (m + 1) / 2;
-  size_t d = (l_in_smem ? P : 0) + 4 * (size_t)n + (n + 1) + (6 + kPanel) * (size_t)m + 320 + 16;
+  size_t d = (l_in_smem ? P : 0) + 4 * (size_t)n + (n + 1) + 6 * (size_t)m +
+             cholesky_scratch(m) + 320 + 16;
   size_t b = d * 8 + align8(sizeof(LanczosScalars)) + 16 * sizeof(int);
   return b;
 }

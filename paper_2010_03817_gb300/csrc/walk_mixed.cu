@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "df.cuh"
 #include "kernels.h"
 #include "lanczos.cuh"
 
@@ -35,7 +36,7 @@ struct MixSmem {
   double* z;      // m
   double* u;      // m
   double* um;     // m (null vector at t-)
-  double* part;   // SPG_WARPS * m
+  double* part;   // SPG_WARPS * m + 64
   double* scr;    // 320
   double* bc;     // 16
   float* q32;     // m
@@ -44,6 +45,14 @@ struct MixSmem {
   float* y32;     // m
   float* ym32;    // m
   float* col32;   // m
+  float* duh;     // m: u as an FP32 pair (stage 2)
+  float* dul;     // m
+  float* dfh;     // m: F u (pair)
+  float* dfl;     // m
+  float* dgh;     // m: V u (pair)
+  float* dgl;     // m
+  float* d32;     // m: residual / correction
+  float* x32;     // m
   LanczosScalars* sc;
   int* ib;        // 16
 };
@@ -68,7 +77,7 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.z = d; d += m;
   s.u = d; d += m;
   s.um = d; d += m;
-  s.part = d; d += (size_t)SPG_WARPS * m;
+  s.part = d; d += (size_t)SPG_WARPS * m + 64;  // also the Cholesky panel
   s.scr = d; d += 320;
   s.bc = d; d += 16;
   float* f = reinterpret_cast<float*>(d);
@@ -77,8 +86,17 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.z32 = f; f += m;
   s.y32 = f; f += m;
   s.ym32 = f; f += m;
-  s.col32 = f; f += m;  // 6 m floats: the next address stays 8-byte aligned
+  s.col32 = f; f += m;
+  s.duh = f; f += m;
+  s.dul = f; f += m;
+  s.dfh = f; f += m;
+  s.dfl = f; f += m;
+  s.dgh = f; f += m;
+  s.dgl = f; f += m;
+  s.d32 = f; f += m;
+  s.x32 = f; f += m;  // 14 m floats: the next address stays 8-byte aligned
   s.sc = reinterpret_cast<LanczosScalars*>(f);
+  if (threadIdx.x == 0) s.sc->prof = nullptr;
   s.ib = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(s.sc) + sizeof(LanczosScalars));
   return s;
 }
@@ -106,21 +124,6 @@ __device__ void normalise_vec(double* u, int m, MixSmem& sm) {
   __syncthreads();
 }
 
-// pencil Rayleigh quotient t = -(u^T F u)/(u^T V u) with F, V packed FP64
-__device__ double pencil_rq(const double* Fg, const double* Vg, const double* u, int m,
-                            MixSmem& sm) {
-  symv_packed<double>(Fg, u, sm.r, m, 1.0, sm.part);
-  symv_packed<double>(Vg, u, sm.z, m, 1.0, sm.part);
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < m; i += SPG_THREADS) {
-    a += u[i] * sm.r[i];
-    b += u[i] * sm.z[i];
-  }
-  a = block_sum(a, sm.sc->red);
-  b = block_sum(b, sm.sc->red);
-  return -a / b;
-}
-
 __device__ __forceinline__ void stage_mark(const MixWork& mw, int stage, long long& t0) {
   if (mw.prof && threadIdx.x == 0) {
     const long long t1 = clock64();
@@ -128,6 +131,246 @@ __device__ __forceinline__ void stage_mark(const MixWork& mw, int stage, long lo
               (unsigned long long)(t1 - t0));
     t0 = t1;
   }
+}
+
+// CTA-wide double-float sum (result on every thread); red: 2 * SPG_WARPS floats
+__device__ __forceinline__ void block_sum_df(float& h, float& l, float* red) {
+  warp_sum_df(h, l);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[2 * wid] = h;
+    red[2 * wid + 1] = l;
+  }
+  __syncthreads();
+  h = 0.f;
+  l = 0.f;
+#pragma unroll
+  for (int w = 0; w < SPG_WARPS; ++w) df_add(h, l, red[2 * w], red[2 * w + 1]);
+  df_norm(h, l);
+}
+
+constexpr int kDfColBlocks = 8;  // column blocks of 32 per pass of symv_df2
+
+// f = F u and g = V u in double-float: F, V packed FP64 (global), u as an FP32
+// pair (uh, ul), results as pairs.  Passes over groups of 8 column blocks of
+// 32; in each, warp w takes the rows r = w, w + 8, ... that reach the group,
+// its lanes the group's columns k <= r of row r: entry (r, k) adds F_rk u_k to
+// the row sum of r and, for k < r, F_rk u_r to the column sum of k (kept per
+// lane in registers, then reduced over the warps through scr:
+// 4 SPG_WARPS 256 floats).  A row's partial sums are added by the warp that
+// owns it, and every entry belongs to the pass of its column, so the passes
+// need no further ordering.
+__device__ void symv_df2(const double* __restrict__ F, const double* __restrict__ V,
+                         const float* uh, const float* ul, int m, float* fh, float* fl, float* gh,
+                         float* gl, float* scr) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kW = 32 * kDfColBlocks;
+  float* s0 = scr;
+  float* s1 = scr + SPG_WARPS * kW;
+  float* s2 = scr + 2 * SPG_WARPS * kW;
+  float* s3 = scr + 3 * SPG_WARPS * kW;
+  for (int k0 = 0; k0 < m; k0 += kW) {
+    float cfh[kDfColBlocks], cfl[kDfColBlocks], cgh[kDfColBlocks], cgl[kDfColBlocks];
+#pragma unroll
+    for (int b = 0; b < kDfColBlocks; ++b) cfh[b] = cfl[b] = cgh[b] = cgl[b] = 0.f;
+    for (int r = k0 + ((wid - k0 % SPG_WARPS + SPG_WARPS) % SPG_WARPS); r < m; r += SPG_WARPS) {
+      const size_t base = tri(r, 0);
+      double fv[kDfColBlocks], vv[kDfColBlocks];
+#pragma unroll
+      for (int b = 0; b < kDfColBlocks; ++b) {
+        const int k = k0 + lane + 32 * b;
+        fv[b] = k <= r ? F[base + k] : 0.0;
+        vv[b] = k <= r ? V[base + k] : 0.0;
+      }
+      const float urh = uh[r], url = ul[r];
+      float rfh = 0.f, rfl = 0.f, rgh = 0.f, rgl = 0.f;
+#pragma unroll
+      for (int b = 0; b < kDfColBlocks; ++b) {
+        const int k = k0 + lane + 32 * b;
+        if (k <= r) {
+          const float2 a = split_df(fv[b]);
+          const float2 c = split_df(vv[b]);
+          const float xh = uh[k], xl = ul[k];
+          df_mac(rfh, rfl, a.x, a.y, xh, xl);
+          df_mac(rgh, rgl, c.x, c.y, xh, xl);
+          if (k < r) {
+            df_mac(cfh[b], cfl[b], a.x, a.y, urh, url);
+            df_mac(cgh[b], cgl[b], c.x, c.y, urh, url);
+          }
+        }
+      }
+      warp_sum_df(rfh, rfl);
+      warp_sum_df(rgh, rgl);
+      if (lane == 0) {
+        if (k0 > 0) {
+          df_add(rfh, rfl, fh[r], fl[r]);
+          df_add(rgh, rgl, gh[r], gl[r]);
+        }
+        fh[r] = rfh;
+        fl[r] = rfl;
+        gh[r] = rgh;
+        gl[r] = rgl;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kDfColBlocks; ++b) {
+      const int q = lane + 32 * b;
+      s0[wid * kW + q] = cfh[b];
+      s1[wid * kW + q] = cfl[b];
+      s2[wid * kW + q] = cgh[b];
+      s3[wid * kW + q] = cgl[b];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kW && k0 + q < m; q += SPG_THREADS) {
+      const int k = k0 + q;
+      float h = fh[k], l = fl[k], h2 = gh[k], l2 = gl[k];
+#pragma unroll
+      for (int w = 0; w < SPG_WARPS; ++w) {
+        df_add(h, l, s0[w * kW + q], s1[w * kW + q]);
+        df_add(h2, l2, s2[w * kW + q], s3[w * kW + q]);
+      }
+      df_norm(h, l);
+      df_norm(h2, l2);
+      fh[k] = h;
+      fl[k] = l;
+      gh[k] = h2;
+      gl[k] = l2;
+    }
+    __syncthreads();
+  }
+}
+
+// pencil Rayleigh quotient t = -(u^T F u)/(u^T V u) with the exact F, V
+// (packed FP64, global) in double-float; stationary at the null vector, so
+// an FP32-accurate u gives t to about FP32 precision squared.  scr: the
+// region after the FP32 factor (4 SPG_WARPS 256 floats).
+__device__ double pencil_rq(const double* Fg, const double* Vg, const double* u, int m,
+                            MixSmem& sm, float* scr) {
+  for (int i = threadIdx.x; i < m; i += SPG_THREADS) {
+    const float2 s = split_df(u[i]);
+    sm.duh[i] = s.x;
+    sm.dul[i] = s.y;
+  }
+  __syncthreads();
+  symv_df2(Fg, Vg, sm.duh, sm.dul, m, sm.dfh, sm.dfl, sm.dgh, sm.dgl, scr);
+  float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+  for (int i = threadIdx.x; i < m; i += SPG_THREADS) {
+    df_mac(ah, al, sm.duh[i], sm.dul[i], sm.dfh[i], sm.dfl[i]);
+    df_mac(bh, bl, sm.duh[i], sm.dul[i], sm.dgh[i], sm.dgl[i]);
+  }
+  float* red = reinterpret_cast<float*>(sm.sc->red);
+  block_sum_df(ah, al, red);
+  block_sum_df(bh, bl, red);
+  return -df_to_double(ah, al) / df_to_double(bh, bl);
+}
+
+// Stage 2 in double-float for one end of the chord (the FP32 pipe; on this
+// GPU the FP64 pipe runs at about 1/58 of its rate).  The factorisation next
+// to the boundary needs more than FP32: F + sigma1 V is within delta of
+// singular, and the LMI's own condition number (10^4 for the Dabbene
+// generator's A_0) would make FP32's backward error exceed its smallest
+// eigenvalue.  Double-float (about 48 bits) leaves a wide margin:
+//   Cholesky of F + sigma1 V, sigma1 = sigma0 + (t_est - sigma0)(1 - delta)
+//   (retries with delta x 8), power iteration on M_sigma1 = -L^{-1} V L^{-T}
+//   from y = L^T u0 (u0 slightly perturbed), certificate as in the FP64
+//   refinement.  u0 (FP64) in sm.u, left untouched unless the result is
+//   kOk: then t and the unit null vector (sm.u).
+__device__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+                             const double* __restrict__ Fg, const double* __restrict__ Vg,
+                             double sigma0, double t_est, double* t, MixResult* res, bool plus,
+                             double delta0, int attempts, int iters) {
+  using T = dfloat;
+  const int tid = threadIdx.x;
+  const int m = sp.m;
+  const long long P = sp.P;
+  T* G = reinterpret_cast<T*>(sm.R);
+  T* y = reinterpret_cast<T*>(sm.y);
+  T* r = reinterpret_cast<T*>(sm.r);
+  T* z = reinterpret_cast<T*>(sm.z);
+  T* part = reinterpret_cast<T*>(sm.part);
+  T* scr = reinterpret_cast<T*>(sm.scr);
+  T* red = reinterpret_cast<T*>(sm.sc->red);
+  long long tmark = clock64();
+  double sigma1 = sigma0;
+  bool ok = false;
+  double delta = delta0;
+  for (int attempt = 0; attempt < attempts && !ok; ++attempt) {
+    sigma1 = sigma0 + (t_est - sigma0) * (1.0 - delta);
+    const T s1(sigma1);
+    for (long long e = tid; e < P; e += SPG_THREADS) G[e] = T(Fg[e]) + s1 * T(Vg[e]);
+    if (tid == 0) sm.ib[0] = 0;
+    __syncthreads();
+    ok = factor_cholesky<T>(G, m, part, &sm.ib[0]);
+    if (!ok) {
+      ++res->retries;
+      delta *= 8.0;
+    }
+  }
+  stage_mark(mw, 2, tmark);  // double-float fill + Cholesky
+  if (!ok) return kNotPD;
+  // start vector u0 + a small deterministic perturbation (every eigenvector
+  // gets a component: a start on the wrong root cannot pass the residual
+  // test by an absent component), then y = L^T u
+  {
+    double a = 0.0;
+    for (int i = tid; i < m; i += SPG_THREADS) a += sm.u[i] * sm.u[i];
+    const double nu = sqrt(block_sum(a, sm.sc->red));
+    const double pert = 1e-6 * nu / sqrt((double)m);
+    for (int i = tid; i < m; i += SPG_THREADS) z[i] = T(sm.u[i] + pert * sin(1.3 * i + 0.7));
+    __syncthreads();
+  }
+  mul_upper<T>(G, z, y, m, part);
+  invert_diag_blocks<T>(G, m);
+  bool converged = false;
+  double mu = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    T a(0);
+    for (int i = tid; i < m; i += SPG_THREADS) a += y[i] * y[i];
+    const T rn = rsqrt_t(block_sum(a, red));
+    for (int i = tid; i < m; i += SPG_THREADS) {
+      y[i] *= rn;
+      z[i] = y[i];
+    }
+    __syncthreads();
+    // r = M y = -L^{-1} V L^{-T} y
+    solve_upper<T>(G, z, m, scr);
+    symv_packed<T, double>(Vg, z, r, m, T(-1), part);
+    solve_lower<T>(G, r, m, scr);
+    T b(0);
+    for (int i = tid; i < m; i += SPG_THREADS) b += y[i] * r[i];
+    const T mut = block_sum(b, red);
+    T c(0);
+    for (int i = tid; i < m; i += SPG_THREADS) {
+      const T d = r[i] - mut * y[i];
+      c += d * d;
+    }
+    const double res2 = to_double(block_sum(c, red));
+    mu = to_double(mut);
+    for (int i = tid; i < m; i += SPG_THREADS) y[i] = r[i];
+    __syncthreads();
+    ++res->power;
+    if (res2 <= mw.tol64 * mw.tol64 * mu * mu) {
+      converged = true;
+      break;
+    }
+  }
+  // certificate: the dominant eigenvalue belongs to this end and its root
+  // lies closer to sigma1 than 0 does (no root of the other side dominates)
+  if (plus ? !(mu > 0.0 && 1.0 / mu < sigma1) : !(mu < 0.0 && -1.0 / mu < -sigma1))
+    converged = false;
+  if (converged) {
+    *t = sigma1 + 1.0 / mu;
+    // u = L^{-T} y
+    for (int i = tid; i < m; i += SPG_THREADS) z[i] = y[i];
+    __syncthreads();
+    solve_upper<T>(G, z, m, scr);
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = to_double(z[i]);
+    __syncthreads();
+    normalise_vec(sm.u, m, sm);
+  }
+  stage_mark(mw, 3, tmark);  // double-float power iterations
+  return converged ? kOk : kNoConv;
 }
 
 // Stage 2 for one end of the chord: FP64 Cholesky of F + sigma1 V with
@@ -161,16 +404,19 @@ __device__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm
     }
   }
   const bool power = ok;
-  if (!ok) {
-    sigma1 = sigma0;
-    for (long long e = tid; e < P; e += SPG_THREADS) G64[e] = Fg[e] + sigma0 * Vg[e];
+  // fall back to a factorisation at sigma0, then at the point itself (sigma =
+  // 0: interior by construction); only if that fails is the point outside S
+  for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+    sigma1 = attempt == 0 ? sigma0 : 0.0;
+    if (attempt == 1 && sigma0 == 0.0) break;
+    for (long long e = tid; e < P; e += SPG_THREADS) G64[e] = Fg[e] + sigma1 * Vg[e];
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
     ok = factor_cholesky<double>(G64, m, sm.part, &sm.ib[0]);
-    if (!ok) {
-      *t = 0.0;
-      return kNotPD;
-    }
+  }
+  if (!ok) {
+    *t = 0.0;
+    return kNotPD;
   }
   stage_mark(mw, 2, tmark);  // FP64 fill + Cholesky
   double mu = 0.0;
@@ -263,8 +509,25 @@ __device__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm
   return converged ? kOk : kNoConv;
 }
 
+// Stage 2 for one end: the double-float refinement, the FP64 one when it
+// does not converge (or without an estimate: cold).  u0 in sm.u.
+__device__ int refine_end(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+                          const double* __restrict__ Fg, const double* __restrict__ Vg,
+                          double* __restrict__ Q64, double sigma0, double t_est, bool cold,
+                          double* t, MixResult* res, bool plus) {
+  if (!cold) {
+    if (refine_end_dd(sp, mw, sm, Fg, Vg, sigma0, t_est, t, res, plus, mw.delta1, 3,
+                      mw.power_iters) == kOk)
+      return kOk;
+    res->fallback = 1;
+  }
+  return refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, t_est, cold, t, res, plus);
+}
+
 // One boundary-oracle evaluation in mixed precision (CTA-wide).
 //   Fg, Vg: packed FP64 F(p) and V (global).  sigma0: stage-1 shift.
+//   pred (learned warm start): the network's (log(t+/t_scale), u) for this
+//   line; the shift sigma1 = (1 - margin) t^ replaces stage 1.
 __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
                                    const double* __restrict__ Fg, const double* __restrict__ Vg,
                                    float* __restrict__ Q32, double* __restrict__ Q64,
@@ -283,71 +546,47 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
   res.t_minus = -INFINITY;
   float* G32 = reinterpret_cast<float*>(sm.R);
   float* V32 = G32 + P;
-  double* G64 = reinterpret_cast<double*>(sm.R);
   long long tmark = clock64();
 
-  // ---------------- stage 1 (learned): shifted power iteration --------------
-  // The network predicts t+ and the null vector u.  Factor F + sigma0 V with
-  // sigma0 = (1 - margin) t^ and iterate on M_sigma0 from L^T u^: its
-  // dominant eigenvalue is 1/(t+ - sigma0).  Accepted when it converges and
-  // t+ - sigma0 < sigma0 (no root below sigma0 can dominate); otherwise the
-  // plain stage 1 below runs.
+  // ---------------- stage 1 with the learned warm start ---------------------
+  // The network predicts t+ and the null vector u.  Stage 1 factors at
+  // sigma0 = (1 - margin) t^ instead (a failed factorisation, t^ too large,
+  // falls back to the plain stage 1) and starts the Lanczos from L^T u^: next
+  // to the boundary the wanted eigenvalue 1/(t+ - sigma0) of M_sigma0
+  // stands apart from the rest, so fewer iterations reach the tolerance
+  // (checked every second step).  Stage 2 certifies and refines as usual.
   double t1 = 0.0, t1m = -INFINITY;
   bool have_t1 = false;
   if (pred && !want_min) {
     const double that = t_scale * exp((double)pred[0]);
-    double sig = that * (1.0 - margin);
+    const double sig = that * (1.0 - margin);
     bool okl = false;
-    for (int attempt = 0; attempt < 2 && !okl && isfinite(sig) && sig > 0.0; ++attempt) {
+    if (isfinite(sig) && sig > 0.0) {
+      const float sf = (float)sig;
       for (long long e = tid; e < P; e += SPG_THREADS) {
-        const double g = Vg[e];
-        G32[e] = (float)(Fg[e] + sig * g);
-        V32[e] = (float)g;
+        const float vh = trunc_f32(Vg[e]);
+        G32[e] = fmaf(sf, vh, trunc_f32(Fg[e]));
+        V32[e] = vh;
       }
       if (tid == 0) sm.ib[0] = 0;
       __syncthreads();
       okl = factor_cholesky<float>(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
-      if (!okl) {
-        ++res.retries;
-        sig *= 0.5;
-      }
+      if (!okl) ++res.retries;
     }
     stage_mark(mw, 0, tmark);
     if (okl) {
       for (int i = tid; i < m; i += SPG_THREADS) sm.z32[i] = pred[1 + i];
       __syncthreads();
-      mul_upper<float>(G32, sm.z32, sm.y32, m, reinterpret_cast<float*>(sm.part));
+      mul_upper<float>(G32, sm.z32, sm.q32, m, reinterpret_cast<float*>(sm.part));
       invert_diag_blocks<float>(G32, m);
       PencilOp<float> op{G32, V32, true, reinterpret_cast<float*>(sm.part)};
-      float mu = 0.f;
-      bool conv = false;
-      for (int it = 0; it < mw.learned_iters; ++it) {
-        float a = 0.f;
-        for (int i = tid; i < m; i += SPG_THREADS) a += sm.y32[i] * sm.y32[i];
-        const float ny = sqrtf(block_sum(a, reinterpret_cast<float*>(sm.sc->red)));
-        for (int i = tid; i < m; i += SPG_THREADS) sm.y32[i] /= ny;
-        __syncthreads();
-        apply_pencil<float>(op, sm.y32, sm.r32, sm.q32, m, reinterpret_cast<float*>(sm.scr));
-        float b = 0.f;
-        for (int i = tid; i < m; i += SPG_THREADS) b += sm.y32[i] * sm.r32[i];
-        mu = block_sum(b, reinterpret_cast<float*>(sm.sc->red));
-        float c = 0.f;
-        for (int i = tid; i < m; i += SPG_THREADS) {
-          const float d = sm.r32[i] - mu * sm.y32[i];
-          c += d * d;
-        }
-        const float resid = sqrtf(block_sum(c, reinterpret_cast<float*>(sm.sc->red)));
-        for (int i = tid; i < m; i += SPG_THREADS) sm.y32[i] = sm.r32[i];
-        __syncthreads();
-        ++res.iters;
-        if (resid <= (float)mw.tol32 * fabsf(mu)) {
-          conv = true;
-          break;
-        }
-      }
-      if (conv && mu > 0.f && 1.0 / mu < sig) {
+      LanczosOut lo = lanczos_extreme<float>(op, Q32, sm.q32, sm.r32, sm.z32,
+                                             reinterpret_cast<float*>(sm.scr), sm.y32, sm.ym32,
+                                             m, mw.kmax32, false, mw.tol32, sm.sc, 4, 2);
+      res.iters += lo.iters;
+      if (lo.converged && lo.theta_max > 0.0) {
         sigma0 = sig;
-        t1 = sig + 1.0 / mu;
+        t1 = sig + 1.0 / lo.theta_max;
         have_t1 = true;
         solve_upper<float>(G32, sm.y32, m, reinterpret_cast<float*>(sm.scr));
         for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = (double)sm.y32[i];
@@ -361,10 +600,11 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
   // ---------------- stage 1: FP32 estimate ---------------------------------
   bool ok = have_t1;
   for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+    const float s0f = (float)sigma0;
     for (long long e = tid; e < P; e += SPG_THREADS) {
-      const double g = Vg[e];
-      G32[e] = (float)(Fg[e] + sigma0 * g);
-      V32[e] = (float)g;
+      const float vh = trunc_f32(Vg[e]);
+      G32[e] = fmaf(s0f, vh, trunc_f32(Fg[e]));
+      V32[e] = vh;
     }
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
@@ -375,7 +615,7 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
     }
   }
   stage_mark(mw, 0, tmark);  // stage 1 fill + FP32 Cholesky
-  int fp64_fallback = !ok;
+  const int fp64_fallback = !ok;
   if (ok && !have_t1) {
     invert_diag_blocks<float>(G32, m);
     for (int i = tid; i < m; i += SPG_THREADS) sm.q32[i] = 1.0f + 0.5f * __sinf(0.7f * i + 0.1f);
@@ -407,25 +647,25 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
   stage_mark(mw, 1, tmark);  // FP32 Lanczos
   if (want_min && isfinite(t1m)) {
     // t- from the FP64 pencil Rayleigh quotient (stationary at the eigenvector)
-    res.t_minus = pencil_rq(Fg, Vg, sm.um, m, sm);
+    res.t_minus = pencil_rq(Fg, Vg, sm.um, m, sm, V32);
     normalise_vec(sm.um, m, sm);
   }
 
   if (!stage2 && !fp64_fallback) {
     // t+ from the FP64 pencil Rayleigh quotient of the stage-1 vector
-    res.t_plus = pencil_rq(Fg, Vg, sm.u, m, sm);
+    res.t_plus = pencil_rq(Fg, Vg, sm.u, m, sm, V32);
     normalise_vec(sm.u, m, sm);
     res.status = kOk;
     return res;
   }
-  // ---------------- stage 2: FP64 factorisation next to the boundary -------
+  // ---------------- stage 2: refinement at each end ------------------------
   if (fp64_fallback) t1 = 0.0;
   if (want_min && isfinite(t1m) && !fp64_fallback) {
-    // t- end: the same refinement on the negative side (u0 of t- is in um)
+    // t- end first (its u0 is in um); the t+ start vector waits in y32
     for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = sm.um[i];
     __syncthreads();
     double tm;
-    int st = refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, t1m, false, &tm, &res, false);
+    const int st = refine_end(sp, mw, sm, Fg, Vg, Q64, sigma0, t1m, false, &tm, &res, false);
     if (st == kOk) {
       res.t_minus = tm;
       for (int i = tid; i < m; i += SPG_THREADS) sm.um[i] = sm.u[i];
@@ -435,31 +675,30 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
     __syncthreads();
   }
   double tp;
-  res.status = refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, fp64_fallback ? 0.0 : t1,
-                               fp64_fallback, &tp, &res);
+  res.status = refine_end(sp, mw, sm, Fg, Vg, Q64, sigma0, t1, fp64_fallback, &tp, &res, true);
   res.t_plus = tp;
   return res;
 }
 
-// w_j = u^T A_j u, j = 0..n, by a double-float contraction over the packed
-// entries: A_j = hi + lo (FP32 pair, precomputed), U = u_i u_k (x2 off the
-// diagonal) as an FP32 pair; each product is split exactly with an FMA and
-// the high parts are summed with TwoSum, the rounding errors of both kept in
-// a separate accumulator (Ogita, Rump, Oishi: Sum2 / Dot2).  Error ~ n eps^2
-// of sum |terms| (eps = 2^-24), returned as hi + lo in FP64.
+// w_j = u^T A_j u, j = 0..n (Lemma "Gradient of det F"), by a double-float
+// contraction over the packed entries: A_j = hi + lo (FP32 pair,
+// precomputed), U = u_i u_k (x2 off the diagonal) as an FP32 pair, formed
+// once in the work region; each product is split exactly with an FMA and the
+// high parts are summed with TwoSum, the rounding errors of both kept in a
+// separate accumulator (Ogita, Rump, Oishi: Sum2 / Dot2).  Error ~ n eps^2 of
+// sum |terms| (eps = 2^-24).  Warp w takes the matrices j = w, w + 8, ...
 __device__ void contract_forms(const DevSpec& sp, const float2* __restrict__ Ahl, MixSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m;
   const long long P = sp.P;
   float* Uh = reinterpret_cast<float*>(sm.R);
   float* Ul = Uh + P;
-  // u as FP32 pairs
-  float* uh = sm.q32;
-  float* ul = sm.r32;
+  float* uh = sm.duh;
+  float* ul = sm.dul;
   for (int i = tid; i < m; i += SPG_THREADS) {
-    const float h = (float)sm.u[i];
-    uh[i] = h;
-    ul[i] = (float)(sm.u[i] - (double)h);
+    const float2 s = split_df(sm.u[i]);
+    uh[i] = s.x;
+    ul[i] = s.y;
   }
   __syncthreads();
   for (long long e = tid; e < P; e += SPG_THREADS) {
@@ -481,19 +720,10 @@ __device__ void contract_forms(const DevSpec& sp, const float2* __restrict__ Ahl
     float acc = 0.f, lo = 0.f;
     for (long long e = lane; e < P; e += 32) {
       const float2 a = Aj[e];
-      const float uh_e = Uh[e], ul_e = Ul[e];
-      const float p = a.x * uh_e;
-      const float pe = fmaf(a.x, uh_e, -p);
-      // TwoSum(acc, p)
-      const float s = acc + p;
-      const float bb = s - acc;
-      const float err = (acc - (s - bb)) + (p - bb);
-      acc = s;
-      lo += err + fmaf(a.x, ul_e, fmaf(a.y, uh_e, pe));
+      df_mac(acc, lo, a.x, a.y, Uh[e], Ul[e]);
     }
-    double tot = (double)acc + (double)lo;
-    tot = warp_sum(tot);
-    if (lane == 0) sm.w[j] = tot;
+    warp_sum_df(acc, lo);
+    if (lane == 0) sm.w[j] = (double)acc + (double)lo;
   }
   __syncthreads();
 }
@@ -536,6 +766,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   const size_t cta = blockIdx.x;
   uint8_t* rg = mw.region_global ? mw.region_global + cta * mw.region_bytes : nullptr;
   MixSmem sm = mix_carve(smem_raw, n, m, rg, mw.region_bytes);
+  if (tid == 0 && mw.prof) sm.sc->prof = mw.prof + blockIdx.x * kProfSlots + 8;
   float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
   double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
   const int count = *wv.count_cur;
@@ -740,6 +971,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   const size_t cta = blockIdx.x;
   uint8_t* rg = mw.region_global ? mw.region_global + cta * mw.region_bytes : nullptr;
   MixSmem sm = mix_carve(smem_raw, n, m, rg, mw.region_bytes);
+  if (tid == 0 && mw.prof) sm.sc->prof = mw.prof + blockIdx.x * kProfSlots + 8;
   float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
   double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
   for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
@@ -805,15 +1037,20 @@ cudaError_t launch_learned_features(const double* X, const double* dir, const in
   return cudaGetLastError();
 }
 
-size_t mixed_region_bytes(int m) {
+size_t mixed_region_bytes(int n, int m) {
+  (void)n;
   const size_t P = (size_t)m * (m + 1) / 2;
-  return P * 8;  // max of 2 P floats (stages 1, 3) and P doubles (stage 2)
+  // max of 2 P floats (stage 1, contraction), P doubles or double-floats
+  // (stage 2) and the FP32 factor plus the column partials of the
+  // double-float products (pencil Rayleigh quotient)
+  const size_t df = (P + 4 * (size_t)SPG_WARPS * 256) * 4;
+  return ((P * 8 > df ? P * 8 : df) + 15) & ~size_t(15);
 }
 
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem) {
-  size_t b = region_in_smem ? ((mixed_region_bytes(m) + 15) & ~size_t(15)) : 0;
-  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 320 + 16);
-  b += 4 * (size_t)6 * m;
+  size_t b = region_in_smem ? ((mixed_region_bytes(n, m) + 15) & ~size_t(15)) : 0;
+  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 64 + 320 + 16);
+  b += 4 * (size_t)14 * m;
   b += sizeof(LanczosScalars) + 16 * sizeof(int);
   return b;
 }

@@ -176,7 +176,7 @@ class Spectrahedron:
                                    t_scale, margin, iters))
 
     def set_stage_timers(self, timers=None):
-        """Mixed-path stage timers: an int64 CUDA tensor (SMs x 8), or None."""
+        """Mixed-path stage timers: an int64 CUDA tensor (SMs x 16), or None."""
         import torch
         _check(lib().sp_set_stage_timers(self._h, _dev(timers, torch.int64) if timers is not None
                                          else None))
