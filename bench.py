@@ -199,19 +199,30 @@ def alg_flops_fp64(n, m, stats, steps):
             + stats["lanczos_iters"] * 4 * m * m)
 
 
-def alg_flops_wave_fp64(n, m, stats):
-    """FP64 flops of the mixed wave kernel: per segment the factorisation next
-    to the boundary (m^3/3), its fill (2P) and the carried-F update (2P); 4m^2
-    per FP64 power iteration."""
+def alg_flops_wave(n, m, stats):
+    """Algorithmic flops of the mixed wave kernel: per segment two Cholesky
+    factorisations (m^3/3 each: FP32 at the stage-1 shift, double-float next to
+    the boundary), their fills (2P each) and the carried-F update (2P); 4m^2
+    per Lanczos or power iteration (two triangular solves and a product with
+    V)."""
     P = m * (m + 1) / 2
-    return stats["segments"] * (m ** 3 / 3 + 4 * P) + stats["power_iters"] * 4 * m * m
+    return (stats["segments"] * (2 * m ** 3 / 3 + 6 * P)
+            + (stats["lanczos_iters"] + stats["power_iters"]) * 4 * m * m)
+
+
+def alg_flops_contraction(n, m, segments):
+    """Tensor-core flops of the digit-split normal contraction: 28 digit pairs
+    of a (rows x 16-padded m) x (m x (n+1) 32-padded m) product per segment."""
+    Kp = (m + 15) // 16 * 16
+    Q = (n + 1) * ((m + 31) // 32 * 32)
+    return segments * 28 * 2 * Kp * Q
 
 
 def alg_flops_formation(n, m, segments):
     """Tensor-core flops of the digit-split formation of V: 28 digit pairs of a
     (rows x 16-padded K) x (K x P) product per segment."""
     P = m * (m + 1) / 2
-    Kp = (n + 1 + 15) // 16 * 16
+    Kp = (n + 15) // 16 * 16
     return segments * 28 * 2 * Kp * P
 
 
@@ -389,14 +400,15 @@ def main():
         ms = kt["fp64_ms"] or head["dev_ms"]
         roof = {"bound": "alu", "kernel": "walk_fp64_kernel",
                 "launches": int(kt["fp64_launches"])}
+        peak, unit = 152 * 2 * 2 * 2.07e9 / 1e12, "TFLOP/s (FP64)"  # 2 DFMA/clk/SM
     else:
-        flops = alg_flops_wave_fp64(N_DIM, M_DIM, st)
+        flops = alg_flops_wave(N_DIM, M_DIM, st)
         ms = kt["wave_ms"] or head["dev_ms"]
         roof = {"bound": "alu", "kernel": "mixed_wave_kernel",
                 "launches": int(kt["wave_launches"])}
-    peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+        peak, unit = 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s (FP32 pipe)"  # 128 FFMA/clk/SM
     achieved = flops / (ms / 1e3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
+    roof.update({"achieved": achieved, "peak": peak, "unit": unit,
                  "frac": achieved / peak, "traffic": None,
                  "kernel_ms_per_step": ms / args.steps,
                  "share_of_step": ms / max(1e-9, head["dev_ms"])})
@@ -409,6 +421,16 @@ def main():
                      "achieved": fa, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": fa / peaks["bf16_tflops"], "peak_source": peaks["source"],
                      "share_of_step": kt["form_ms"] / max(1e-9, head["dev_ms"])}
+    contraction = None
+    if args.mode != "fp64" and kt.get("contract_ms", 0) > 0:
+        cf = alg_flops_contraction(N_DIM, M_DIM, st["segments"])
+        ca = cf / (kt["contract_ms"] / 1e3) / 1e12
+        peaks = _peaks()
+        contraction = {"bound": "tensor", "kernel": "ozaki_kernel<contract> (+ digit slicing)",
+                       "achieved": ca, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                       "frac": ca / peaks["bf16_tflops"], "peak_source": peaks["source"],
+                       "share_of_step": kt["contract_ms"] / max(1e-9, head["dev_ms"]),
+                       "finish_share_of_step": kt["finish_ms"] / max(1e-9, head["dev_ms"])}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -469,7 +491,8 @@ def main():
         if "fp64" in paths and args.mode != "fp64":
             speedup = paths[args.mode]["steps_per_s"] / paths["fp64"]["steps_per_s"]
         launches = int(kt["fp64_launches"] + kt["form_launches"] + kt["wave_launches"]
-                       + kt["mlp_launches"] + kt["other_launches"])
+                       + kt["mlp_launches"] + kt["other_launches"] + kt["contract_launches"]
+                       + kt["finish_launches"])
         line = {
             "metric": "billiard steps/s at n=m=200",
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -489,6 +512,7 @@ def main():
             "stage_share": head["share"],
             "roofline": roof,
             "roofline_formation": formation,
+            "roofline_contraction": contraction,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -236,6 +236,12 @@ int sp_mlp_create(int din, int dh, int dout, uint64_t seed, sp_mlp** out);
 int sp_mlp_destroy(sp_mlp* q);
 int sp_mlp_dims(const sp_mlp* q, int* din, int* dh, int* dout, long long* nparams);
 int sp_mlp_params(sp_mlp* q, float* host_out, const float* host_in);
+/* Save the network to a file (a small header with the dimensions, then the
+ * FP32 parameters in the layout above) / create a network from such a file
+ * (`seed` only initialises the optimiser state's generator; the Adam
+ * moments start at zero).  SP_EINVAL on I/O errors or a malformed file. */
+int sp_mlp_save(sp_mlp* q, const char* path);
+int sp_mlp_load(const char* path, uint64_t seed, sp_mlp** out);
 int sp_mlp_forward(sp_mlp* q, int count, const float* X, float* Y, void* stream);
 int sp_mlp_gradients(sp_mlp* q, int count, const float* X, const float* T, float* grads_host,
                      float* loss_host, void* stream);
@@ -268,12 +274,14 @@ int sp_record_tuples(sp_chains* ch, float* x_out, float* y_out, int capacity, in
 /*
  * Per-kernel timing of later walk calls on `ch` (CUDA events recorded on the
  * walk's stream around each launch; the mixed path reads them between its
- * waves, the FP64 path at the end of the call).  out (host, 9 doubles, may
+ * waves, the FP64 path at the end of the call).  out (host, 13 doubles, may
  * be NULL): [0] FP64 walk kernel ms, [1] its launches, [2] tensor-core
  * formation ms, [3] its launches (digit slicing + GEMM), [4] mixed wave
  * kernel ms, [5] its launches, [6] warm-start network ms, [7] its launches,
- * [8] other launches.  enable: 1 on (counters reset), 0 off (reset), -1 read
- * only.
+ * [8] other launches, [9] tensor-core normal contraction ms (Billiard),
+ * [10] its launches (digit slicing + GEMM), [11] reflection finish kernel
+ * ms, [12] its launches.  enable: 1 on (counters reset), 0 off (reset), -1
+ * read only.
  */
 int sp_kernel_timing(sp_chains* ch, int enable, double* out);
 

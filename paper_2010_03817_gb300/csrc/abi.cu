@@ -125,12 +125,42 @@ struct MixSpace {
   double* Frows = nullptr;    // rows x P
   double* Vrows = nullptr;    // rows x P
   int* err = nullptr;
+  // deferred normals of a wave (tensor-core contraction)
+  double* Ubuf = nullptr;     // rows x m
+  double* Tbuf = nullptr;     // rows
+  int* pend = nullptr;        // rows
+  double* Wpart = nullptr;    // rows x (n+1) x wtiles
+  void* udig = nullptr;       // 7 x rows x Kp(m) BF16 digits of the null vectors
+  int* uerow = nullptr;       // rows
+  int wtiles = 0;
   void release() {
     cudaFree(Q32); cudaFree(Q64); cudaFree(region); cudaFree(digits); cudaFree(erow);
     cudaFree(Frows); cudaFree(Vrows); cudaFree(err);
+    cudaFree(Ubuf); cudaFree(Tbuf); cudaFree(pend); cudaFree(Wpart); cudaFree(udig);
+    cudaFree(uerow);
     Q32 = nullptr; Q64 = nullptr; region = nullptr; digits = nullptr; erow = nullptr;
     Frows = Vrows = nullptr; err = nullptr;
+    Ubuf = Tbuf = Wpart = nullptr; pend = nullptr; udig = nullptr; uerow = nullptr;
     ctas = rows = 0;
+  }
+  int ensure_contract(int rows_) {
+    if (Ubuf) return SP_OK;
+    wtiles = ozaki_mpad(m) / 32;
+    bool ok = cudaMalloc(&Ubuf, sizeof(double) * (size_t)rows_ * m) == cudaSuccess &&
+              cudaMalloc(&Tbuf, sizeof(double) * rows_) == cudaSuccess &&
+              cudaMalloc(&pend, sizeof(int) * rows_) == cudaSuccess &&
+              cudaMalloc(&Wpart, sizeof(double) * (size_t)rows_ * (n + 1) * wtiles) ==
+                  cudaSuccess &&
+              cudaMalloc(&udig, ozaki_row_bytes(rows_, m)) == cudaSuccess &&
+              cudaMalloc(&uerow, sizeof(int) * rows_) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaFree(Ubuf); cudaFree(Tbuf); cudaFree(pend); cudaFree(Wpart); cudaFree(udig);
+      cudaFree(uerow);
+      Ubuf = Tbuf = Wpart = nullptr; pend = nullptr; udig = nullptr; uerow = nullptr;
+      return fail(SP_ENOMEM, "normal contraction work space allocation failed%s");
+    }
+    return SP_OK;
   }
   int ensure(int n_, int m_, int ctas_, int rows_, int kmax32, int kmax64, bool with_f) {
     if (ctas >= ctas_ && rows >= rows_ && m == m_ && n == n_ && (!with_f || Frows)) return SP_OK;
@@ -174,6 +204,8 @@ struct sp_spec {
   uint16_t* Bsl = nullptr;
   int* ecol = nullptr;
   float2* Ahl = nullptr;
+  uint16_t* Bc = nullptr;  // digits of the rows (j, i) of A_j: tensor-core normals
+  int* ecolc = nullptr;
   int kmax32 = 96, kmax64 = 96, power_iters = 8;
   double tol32 = 1e-5, tol64 = 1e-12, delta1 = 2e-4;
   long long* prof = nullptr;  // optional stage timers (device, ctas x kProfSlots)
@@ -239,7 +271,9 @@ struct sp_chains {
   // optional per-kernel timing of walk calls (CUDA events on the walk's stream)
   bool timing = false;
   double t_form_ms = 0.0, t_wave_ms = 0.0, t_mlp_ms = 0.0, t_fp64_ms = 0.0;
+  double t_contract_ms = 0.0, t_finish_ms = 0.0;
   long long n_form = 0, n_wave = 0, n_mlp = 0, n_fp64 = 0, n_other = 0;
+  long long n_contract = 0, n_finish = 0;
   // tuple recording (caller buffers)
   float* rec_x = nullptr;
   float* rec_y = nullptr;
@@ -348,6 +382,19 @@ int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_sp
       s->mixed_ok = true;
     }
   }
+  // tensor-core normals: digits of the rows of the full A_j (K = m)
+  if (s->mixed_ok && m <= kOzakiMaxK) {
+    const long long Q = (long long)(n + 1) * ozaki_mpad(m);
+    bool ok = cudaMalloc(&s->Bc, ozaki_contract_bytes(n, m)) == cudaSuccess &&
+              cudaMalloc(&s->ecolc, sizeof(int) * Q) == cudaSuccess &&
+              launch_ozaki_slice_full(s->A, n, m, P, s->Bc, s->ecolc, 0) == cudaSuccess &&
+              cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaFree(s->Bc); cudaFree(s->ecolc);
+      s->Bc = nullptr; s->ecolc = nullptr;
+    }
+  }
   *out = s;
   return SP_OK;
 }
@@ -358,6 +405,8 @@ int sp_destroy_spectrahedron(sp_spec* s) {
   cudaFree(s->pidx);
   cudaFree(s->Bsl);
   cudaFree(s->ecol);
+  cudaFree(s->Bc);
+  cudaFree(s->ecolc);
   cudaFree(s->Ahl);
   s->ms.release();
   s->ws.release();
@@ -418,8 +467,22 @@ static int run_prim_mixed(sp_spec* s, PrimParams& pp, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   r = form_rows_mixed(s, s->ms, pp.count, pp.x, pp.v, s->ms.Frows, s->ms.Vrows, st);
   if (r) return r;
+  // reflect: the normals of all lines in one tensor-core contraction
+  const bool tc_normals = pp.op == 1 && s->Bc != nullptr;
+  if (tc_normals) {
+    if (int rr = s->ms.ensure_contract(pp.count)) return rr;
+    pp.Ubuf = s->ms.Ubuf;
+    pp.Wpart = s->ms.Wpart;
+    pp.wtiles = s->ms.wtiles;
+  }
   cudaError_t e = launch_prim_mixed(s->dev(), s->mixwork(s->ms), pp, s->ms.Frows, s->ms.Vrows, st);
   if (e != cudaSuccess) return cuda_fail(e, "mixed boundary-oracle kernel launch");
+  if (tc_normals) {
+    e = launch_ozaki_contract(s->ms.Ubuf, pp.count, s->n, s->m, s->Bc, s->ecolc, s->ms.udig,
+                              s->ms.uerow, s->ms.Wpart, s->ms.err, st);
+    if (e == cudaSuccess) e = launch_prim_reflect_finish(s->dev(), pp, 4 * device_sms(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core normal contraction launch");
+  }
   return SP_OK;
 }
 
@@ -517,11 +580,17 @@ int sp_kernel_timing(sp_chains* ch, int enable, double* out) {
     out[6] = ch->t_mlp_ms;
     out[7] = (double)ch->n_mlp;
     out[8] = (double)ch->n_other;
+    out[9] = ch->t_contract_ms;
+    out[10] = (double)ch->n_contract;
+    out[11] = ch->t_finish_ms;
+    out[12] = (double)ch->n_finish;
   }
   if (enable >= 0) {
     ch->timing = enable != 0;
     ch->t_fp64_ms = ch->t_form_ms = ch->t_wave_ms = ch->t_mlp_ms = 0.0;
+    ch->t_contract_ms = ch->t_finish_ms = 0.0;
     ch->n_fp64 = ch->n_form = ch->n_wave = ch->n_mlp = ch->n_other = 0;
+    ch->n_contract = ch->n_finish = 0;
   }
   return SP_OK;
 }
@@ -724,6 +793,17 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
   wv.rec_y = ch->rec_y;
   wv.rec_count = ch->rec_count;
   wv.rec_cap = ch->rec_cap;
+  // Billiard: the reflections' normals on the tensor cores, one contraction
+  // per wave (deferred from the wave kernel to a finish kernel)
+  const bool defer = kind == 0 && s->Bc != nullptr;
+  if (defer) {
+    if (int r = ch->ms.ensure_contract(ch->C)) return r;
+    wv.Ubuf = ch->ms.Ubuf;
+    wv.Tbuf = ch->ms.Tbuf;
+    wv.pend = ch->ms.pend;
+    wv.Wpart = ch->ms.Wpart;
+    wv.wtiles = ch->ms.wtiles;
+  }
   int cur = 0;
   wv.id_cur = ch->ids[0];
   wv.dir_cur = ch->dirs[0];
@@ -771,17 +851,33 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
     if (ch->timing) cudaEventRecord(ev[3], st);
     ch->n_wave += 1;
     if (e != cudaSuccess) return cuda_fail(e, "walk wave launch");
+    if (defer) {
+      e = launch_ozaki_contract(ch->ms.Ubuf, count, s->n, s->m, s->Bc, s->ecolc, ch->ms.udig,
+                                ch->ms.uerow, ch->ms.Wpart, ch->ms.err, st);
+      if (ch->timing) cudaEventRecord(ev[4], st);
+      if (e == cudaSuccess) e = launch_mixed_reflect(ds, wv, count, 4 * device_sms(), st);
+      if (ch->timing) cudaEventRecord(ev[5], st);
+      ch->n_contract += 2;  // digit slicing + tensor-core GEMM
+      ch->n_finish += 1;
+      if (e != cudaSuccess) return cuda_fail(e, "normal contraction / reflection launch");
+    }
     cur ^= 1;
     if (ch->timing) {
       // the next wave's count copy synchronises the stream; read this wave's events
-      cudaEventSynchronize(ev[3]);
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      cudaEventSynchronize(defer ? ev[5] : ev[3]);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
       cudaEventElapsedTime(&a0, ev[0], ev[1]);
       cudaEventElapsedTime(&a1, ev[1], ev[2]);
       cudaEventElapsedTime(&a2, ev[2], ev[3]);
+      if (defer) {
+        cudaEventElapsedTime(&a3, ev[3], ev[4]);
+        cudaEventElapsedTime(&a4, ev[4], ev[5]);
+      }
       ch->t_form_ms += a0;
       ch->t_mlp_ms += a1;
       ch->t_wave_ms += a2;
+      ch->t_contract_ms += a3;
+      ch->t_finish_ms += a4;
     }
   }
   if (ch->timing)

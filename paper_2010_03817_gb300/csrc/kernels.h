@@ -80,6 +80,11 @@ struct PrimParams {
   double* s;         // count x n (reflect)
   int* status;       // count
   int* inside;       // count (membership)
+  // mixed reflect with the tensor-core normals: null vectors out (count x m,
+  // zero rows where the oracle failed), then partial sums of w_j in
+  double* Ubuf;
+  const double* Wpart;
+  int wtiles;
 };
 
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem);
@@ -129,6 +134,13 @@ struct MixWave {
   int* rec_count;
   int rec_cap;
   double x_scale;
+  // deferred normals (tensor-core contraction of the whole wave): per slot
+  // the null vector (count x m), t+ and a pending flag; null: in-kernel
+  double* Ubuf;
+  double* Tbuf;
+  int* pend;
+  const double* Wpart;  // slot x (n+1) x wtiles partial sums of w_j
+  int wtiles;
 };
 
 size_t mixed_region_bytes(int n, int m);
@@ -136,6 +148,10 @@ cudaError_t launch_learned_features(const double* X, const double* dir, const in
                                     int n, double x_scale, float* feats, cudaStream_t st);
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem);
 cudaError_t launch_mixed_begin(const DevSpec& sp, const MixWave& wv, cudaStream_t st);
+cudaError_t launch_mixed_reflect(const DevSpec& sp, const MixWave& wv, int count, int ctas,
+                                 cudaStream_t st);
+cudaError_t launch_prim_reflect_finish(const DevSpec& sp, const PrimParams& pp, int ctas,
+                                       cudaStream_t st);
 cudaError_t launch_mixed_wave(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
                               cudaStream_t st);
 cudaError_t launch_prim_mixed(const DevSpec& sp, const MixWork& mw, const PrimParams& pp,
@@ -152,7 +168,18 @@ void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, 
 cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const double* A0,
                               const uint16_t* Bsl, const int* ecol, long long P, void* row_digits,
                               int* erow, double* Y, long long ldy, int* err, cudaStream_t st);
-constexpr int kOzakiMaxK = 224;  // n limit of the tensor-core formation
+constexpr int kOzakiMaxK = 224;  // n limit of the tensor-core formation (m for the contraction)
+// the normal forms w_j = u^T A_j u of R null vectors on the tensor cores:
+// (A_j u)_i by the same digit-split GEMM over the rows (j, i) of the full
+// matrices (K = m), folded with u_i into per-tile partial sums
+// Wpart[(r (n+1) + j) (ozaki_mpad(m) / 32) + tile]
+int ozaki_mpad(int m);
+size_t ozaki_contract_bytes(int n, int m);
+cudaError_t launch_ozaki_slice_full(const double* A, int n, int m, long long P, uint16_t* Bc,
+                                    int* ecolc, cudaStream_t st);
+cudaError_t launch_ozaki_contract(const double* U, int R, int n, int m, const uint16_t* Bc,
+                                  const int* ecolc, void* row_digits, int* erow, double* Wpart,
+                                  int* err, cudaStream_t st);
 
 // BF16 GEMM on tcgen05: C = A B^T (+ bias) (ReLU); FP32 and / or BF16 output
 cudaError_t launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,

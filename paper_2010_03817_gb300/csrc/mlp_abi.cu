@@ -3,6 +3,8 @@
 // arithmetic runs in gemm_tc.cu (tcgen05 GEMMs) and mlp.cu (elementwise).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <random>
 #include <vector>
@@ -279,6 +281,58 @@ int sp_mlp_params(sp_mlp* q, float* host_out, const float* host_in) {
         mlp_sync_weights(q, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
       return mlp_fail(SP_ECUDA, "sp_mlp_params: upload failed");
   }
+  return SP_OK;
+}
+
+// file format: 8-byte magic "SPMLP\0\1\0", int32 din, dh, dout, int64 number
+// of parameters, then the FP32 parameters (little-endian, the layout of
+// sp_mlp_params)
+static const char kMlpMagic[8] = {'S', 'P', 'M', 'L', 'P', 0, 1, 0};
+
+int sp_mlp_save(sp_mlp* q, const char* path) {
+  if (!q || !path) return mlp_fail(SP_EINVAL, "sp_mlp_save: null argument");
+  const long long n = (long long)q->offs[6];
+  std::vector<float> h((size_t)n);
+  if (int r = sp_mlp_params(q, h.data(), nullptr)) return r;
+  FILE* f = fopen(path, "wb");
+  if (!f) return mlp_fail(SP_EINVAL, "sp_mlp_save: cannot open the file");
+  const int32_t dims[3] = {q->din, q->dh, q->dout};
+  bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(dims, sizeof(int32_t), 3, f) == 3 &&
+            fwrite(&n, sizeof(n), 1, f) == 1 &&
+            fwrite(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  ok = (fclose(f) == 0) && ok;
+  return ok ? SP_OK : mlp_fail(SP_EINVAL, "sp_mlp_save: write failed");
+}
+
+int sp_mlp_load(const char* path, uint64_t seed, sp_mlp** out) {
+  if (!path || !out) return mlp_fail(SP_EINVAL, "sp_mlp_load: null argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return mlp_fail(SP_EINVAL, "sp_mlp_load: cannot open the file");
+  char magic[8];
+  int32_t dims[3];
+  long long n = 0;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMlpMagic, 8) == 0 &&
+            fread(dims, sizeof(int32_t), 3, f) == 3 && fread(&n, sizeof(n), 1, f) == 1 &&
+            n > 0 && n < (1ll << 34);
+  std::vector<float> h;
+  if (ok) {
+    h.resize((size_t)n);
+    ok = fread(h.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+  }
+  fclose(f);
+  if (!ok) return mlp_fail(SP_EINVAL, "sp_mlp_load: not a network file or truncated");
+  sp_mlp* q = nullptr;
+  if (int r = sp_mlp_create(dims[0], dims[1], dims[2], seed, &q)) return r;
+  if ((long long)q->offs[6] != n) {
+    sp_mlp_destroy(q);
+    return mlp_fail(SP_EINVAL, "sp_mlp_load: parameter count does not match the dimensions");
+  }
+  if (int r = sp_mlp_params(q, nullptr, h.data())) {
+    sp_mlp_destroy(q);
+    return r;
+  }
+  *out = q;
   return SP_OK;
 }
 

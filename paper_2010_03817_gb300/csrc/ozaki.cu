@@ -103,11 +103,28 @@ __global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, 
   }
 }
 
+// Epilogue of the digit-split GEMM.  kForm: Y[r][p] = value (+ lead A0[p]).
+// kContract: the rows of B are the rows (j, i) of the full matrices A_j,
+// padded to mpad rows per j (a tile of 32 never straddles two j), and the
+// value is (A_j u_r)_i; the epilogue folds it with u_r[i] into the partial
+// sum of w_j = u_r^T A_j u_r over the tile's 32 rows, written to
+// Wpart[(r n1 + j) (mpad / 32) + tile] (no atomics: a fixed summation order).
+constexpr int kForm = 0, kContract = 1;
+struct OzEpi {
+  const double* A0;
+  double lead;
+  double* Y;
+  long long ldy;
+  const double* U;
+  int m, mpad, n1;
+  double* Wpart;
+};
+
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
-    ozaki_form_kernel(const __nv_bfloat16* __restrict__ Asl, const int* __restrict__ erow, int R,
-                      const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ ecol,
-                      long long P, int Kp, const double* __restrict__ A0, double lead,
-                      double* __restrict__ Y, long long ldy, int* err) {
+    ozaki_kernel(const __nv_bfloat16* __restrict__ Asl, const int* __restrict__ erow, int R,
+                 const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ ecol, long long P,
+                 int Kp, OzEpi ep, int* err) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int kgroups = Kp / 8;
@@ -119,8 +136,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sA1 + a_bytes);  // 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
 
-  const long long p0 = (long long)blockIdx.x * kTileN;
-  const int r0 = blockIdx.y * kTileM;
+  // formation: column tiles along x; contraction: row tiles along x, so that
+  // consecutive blocks share (and the L2 keeps) the same B tile
+  const long long p0 = (long long)(kMode == kForm ? blockIdx.x : blockIdx.y) * kTileN;
+  const int r0 = (kMode == kForm ? blockIdx.y : blockIdx.x) * kTileM;
 
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -193,6 +212,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = r0 + wid * 32 + lane;
     const int er = (r < R) ? erow[r] : 0;
     const uint32_t lane_base = tmem + ((uint32_t)(wid * 32) << 16);
+    double part = 0.0;  // kContract
+    const int jc = kMode == kContract ? (int)(p0 / ep.mpad) : 0;
+    const int i0 = kMode == kContract ? (int)(p0 % ep.mpad) : 0;
     for (int c0 = 0; c0 < kTileN; c0 += 16) {
       long long hi[16], lo[16];
 #pragma unroll
@@ -213,24 +235,78 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (r < R) {
-        double* yrow = Y + (size_t)r * ldy;
+        // hi carries digit sums d = 0..3, lo d = 4..6:
+        //   value = 2^(e - 56) (hi 2^21 + lo), one rounding (integer ops)
+        if (kMode == kForm) {
+          double* yrow = ep.Y + (size_t)r * ep.ldy;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const long long p = p0 + c0 + i;
-          if (p < P) {
-            // hi carries digit sums d = 0..3, lo d = 4..6:
-            //   Y = 2^(e - 56) (hi 2^21 + lo), one rounding (integer ops)
-            const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
-                                            er + ecol[p] - 56);
-            yrow[p] = lead != 0.0 ? fma(lead, A0[p], y) : y;
+          for (int i = 0; i < 16; ++i) {
+            const long long p = p0 + c0 + i;
+            if (p < P) {
+              const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
+                                              er + ecol[p] - 56);
+              yrow[p] = ep.lead != 0.0 ? fma(ep.lead, ep.A0[p], y) : y;
+            }
+          }
+        } else {
+          const double* ur = ep.U + (size_t)r * ep.m;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int ii = i0 + c0 + i;
+            if (ii < ep.m) {
+              const long long p = p0 + c0 + i;
+              const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
+                                              er + ecol[p] - 56);
+              part = fma(y, ur[ii], part);
+            }
           }
         }
       }
     }
+    if (kMode == kContract && r < R)
+      ep.Wpart[((size_t)r * ep.n1 + jc) * (ep.mpad / kTileN) + i0 / kTileN] = part;
   }
   tc::fence_before_sync();
   __syncthreads();
   if (wid == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// one warp per row q = (j, i) of the contraction stack: exponent and digits
+// of the row i of A_j (packed stack, FP64) over k = 0..m-1; rows i >= m of
+// the padding are zero
+__global__ void slice_full_kernel(const double* __restrict__ A, int n1, int m, long long P,
+                                  int mpad, int Kp, __nv_bfloat16* __restrict__ out,
+                                  int* __restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const long long Q = (long long)n1 * mpad;
+  const long long q = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= Q) return;
+  const int j = (int)(q / mpad), i = (int)(q % mpad);
+  const double* Aj = A + (size_t)j * P;
+  double mx = 0.0;
+  if (i < m)
+    for (int k = lane; k < m; k += 32) mx = fmax(mx, fabs(Aj[i >= k ? tri(i, k) : tri(k, i)]));
+  mx = warp_max(mx);
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);
+    e += 1;
+  }
+  if (lane == 0) ex[q] = e;
+  for (int k = lane; k < Kp; k += 32) {
+    double y = (i < m && k < m) ? ldexp(Aj[i >= k ? tri(i, k) : tri(k, i)], -e) : 0.0;
+#pragma unroll
+    for (int s = 0; s < kDigits; ++s) {
+      y *= 128.0;
+      const double d = rint(y);
+      y -= d;
+      out[((size_t)s * Q + q) * Kp + k] = __float2bfloat16_rn((float)d);
+    }
+  }
+}
+
+inline size_t ozaki_smem(int Kp) {
+  return (size_t)kDigits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
 }
 
 }  // namespace
@@ -278,14 +354,58 @@ cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, cons
   slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, Kp, Asl, erow);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)kDigits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
-  e = cudaFuncSetAttribute(ozaki_form_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = ozaki_smem(Kp);
+  e = cudaFuncSetAttribute(ozaki_kernel<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
+  OzEpi ep{};
+  ep.A0 = A0;
+  ep.lead = lead;
+  ep.Y = Y;
+  ep.ldy = ldy;
   dim3 grid((unsigned)((P + kTileN - 1) / kTileN), (unsigned)((R + kTileM - 1) / kTileM));
-  ozaki_form_kernel<<<grid, kThreads, smem, st>>>(
-      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, A0, lead, Y, ldy,
-      err);
+  ozaki_kernel<kForm><<<grid, kThreads, smem, st>>>(
+      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, ep, err);
+  return cudaGetLastError();
+}
+
+int ozaki_mpad(int m) { return (m + kTileN - 1) / kTileN * kTileN; }
+
+size_t ozaki_contract_bytes(int n, int m) {
+  return (size_t)kDigits * (size_t)(n + 1) * ozaki_mpad(m) * ozaki_kp(m) * 2;
+}
+
+cudaError_t launch_ozaki_slice_full(const double* A, int n, int m, long long P, uint16_t* Bc,
+                                    int* ecolc, cudaStream_t st) {
+  const long long Q = (long long)(n + 1) * ozaki_mpad(m);
+  slice_full_kernel<<<(unsigned)((Q + 7) / 8), 256, 0, st>>>(
+      A, n + 1, m, P, ozaki_mpad(m), ozaki_kp(m), reinterpret_cast<__nv_bfloat16*>(Bc), ecolc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_contract(const double* U, int R, int n, int m, const uint16_t* Bc,
+                                  const int* ecolc, void* row_digits, int* erow, double* Wpart,
+                                  int* err, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const int Kp = ozaki_kp(m), mpad = ozaki_mpad(m);
+  __nv_bfloat16* Asl = static_cast<__nv_bfloat16*>(row_digits);
+  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(U, R, m, Kp, Asl, erow);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = ozaki_smem(Kp);
+  e = cudaFuncSetAttribute(ozaki_kernel<kContract>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  OzEpi ep{};
+  ep.U = U;
+  ep.m = m;
+  ep.mpad = mpad;
+  ep.n1 = n + 1;
+  ep.Wpart = Wpart;
+  const long long Q = (long long)(n + 1) * mpad;
+  dim3 grid((unsigned)((R + kTileM - 1) / kTileM), (unsigned)(Q / kTileN));
+  ozaki_kernel<kContract><<<grid, kThreads, smem, st>>>(
+      Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bc), ecolc, Q, Kp, ep, err);
   return cudaGetLastError();
 }
 

@@ -754,6 +754,119 @@ __device__ void draw_direction(uint64_t seed, uint32_t chain, uint32_t step, dou
   __syncthreads();
 }
 
+// Completes the segment of chain c (slot r of this wave) from the oracle's
+// result: the Billiard move or reflection (Alg. 5, Eq. "reflection"; sm.w
+// holds w_j = u^T A_j u, j = 0..n, when t+ < ell), the Hit-and-Run move
+// (Alg. 4), a rejected step (back to its start, F re-formed), the carried F,
+// the end of a step (next direction and length) and the queue of the next
+// wave.  sm.p, sm.v: the chain's point and direction.
+__device__ void complete_segment(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
+                                 MixSmem& sm, int r, int c, int status, double t_plus,
+                                 double t_minus, double ell, int nrefl, double* __restrict__ Fc,
+                                 const double* __restrict__ Vr, long long* st) {
+  const int tid = threadIdx.x;
+  const int n = sp.n;
+  const long long P = sp.P;
+  const uint32_t chain = wv.chain0 + (uint32_t)c;
+  (void)r;
+  bool step_done = false, rejected = false;
+  double move = 0.0;
+  if (wv.kind == 0) {
+    if (status == kOk && t_plus < ell) {
+      const double nw = mix_unit_normal(sm, n);
+      if (!(nw > 0.0)) {
+        status = kDegenerate;
+      } else {
+        double a = 0.0;
+        for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.wh[j];
+        const double vw = block_sum(a, sm.sc->red);
+        move = (1.0 - wv.kappa) * t_plus;
+        for (int j = tid; j < n; j += SPG_THREADS) {
+          sm.p[j] += move * sm.v[j];
+          sm.v[j] -= 2.0 * vw * sm.wh[j];
+        }
+        ell -= t_plus;
+        ++nrefl;
+        if (tid == 0) st[kStatReflections] += 1;
+        if (nrefl > wv.rho) {
+          status = kRho;
+        }
+      }
+    } else if (status == kOk) {
+      move = ell;
+      for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += ell * sm.v[j];
+      step_done = true;
+    }
+  } else {
+    if (status == kOk && !(isfinite(t_plus) && isfinite(t_minus))) status = kUnbounded;
+    if (status == kOk) {
+      const double eta = rng_uniform(wv.seed, chain, wv.step0 + wv.done[c], kStreamEta);
+      move = t_minus + eta * (t_plus - t_minus);
+      for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += move * sm.v[j];
+      step_done = true;
+    }
+  }
+  __syncthreads();
+  long long tu0 = clock64();
+  if (status != kOk) {
+    // the step is rejected: back to its start point; F(x) is re-formed
+    rejected = true;
+    step_done = true;
+    for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] = wv.Xstart[(size_t)c * n + j];
+    __syncthreads();
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const double* Ae = sp.A + e;
+      double f = Ae[0];
+      for (int j = 0; j < n; ++j) f += sm.p[j] * Ae[(size_t)(j + 1) * P];
+      Fc[e] = f;
+    }
+    if (tid == 0) {
+      st[kStatBadSteps] += 1;
+      wv.status[c] = status;
+    }
+  } else if (move != 0.0) {
+    // carried F: F(p + move v) = F(p) + move V
+    for (long long e = tid; e < P; e += SPG_THREADS) Fc[e] += move * Vr[e];
+  }
+  __syncthreads();
+  int done = wv.done[c];
+  if (step_done) {
+    ++done;
+    nrefl = 0;
+    ell = 0.0;
+    for (int j = tid; j < n; j += SPG_THREADS) wv.Xstart[(size_t)c * n + j] = sm.p[j];
+    if (done < wv.steps) {
+      const uint32_t stp = wv.step0 + (uint32_t)done;
+      if (wv.kind == 2) {
+        const double uc = rng_uniform(wv.seed, chain, stp, kStreamCoord);
+        int jc = (int)(uc * n);
+        jc = jc < n ? jc : n - 1;
+        for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = (j == jc) ? 1.0 : 0.0;
+        __syncthreads();
+      } else {
+        draw_direction(wv.seed, chain, stp, sm.v, n, sm);
+      }
+      if (wv.kind == 0) ell = -wv.tau * log(rng_uniform(wv.seed, chain, stp, kStreamEta));
+    }
+  }
+  for (int j = tid; j < n; j += SPG_THREADS) wv.X[(size_t)c * n + j] = sm.p[j];
+  if (done < wv.steps) {
+    // still active: queue the chain (and its direction) for the next wave
+    if (tid == 0) sm.ib[1] = atomicAdd(wv.count_next, 1);
+    __syncthreads();
+    const int slot = sm.ib[1];
+    for (int j = tid; j < n; j += SPG_THREADS) wv.dir_next[(size_t)slot * n + j] = sm.v[j];
+    if (tid == 0) wv.id_next[slot] = c;
+  }
+  stage_mark(mw, 6, tu0);  // F update, next direction, queueing
+  if (tid == 0) {
+    wv.done[c] = done;
+    wv.ell[c] = ell;
+    wv.nrefl[c] = nrefl;
+    wv.tprev[c] = (rejected || step_done) ? 0.0 : t_plus;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // walk: one segment per active chain per launch (wave)
 // ---------------------------------------------------------------------------
@@ -817,106 +930,65 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       if (res.status == kNoConv) st[kStatNoConv] += 1;
     }
     if (res.status == kNoConv) res.status = kOk;
-    int status = res.status;
-    bool step_done = false, rejected = false;
-    double move = 0.0;
-    if (wv.kind == 0) {
-      if (status == kOk && res.t_plus < ell) {
-        long long tc0 = clock64();
-        contract_forms(sp, mw.Ahl, sm);
-        stage_mark(mw, 5, tc0);  // normal contraction
-        const double nw = mix_unit_normal(sm, n);
-        if (!(nw > 0.0)) {
-          status = kDegenerate;
-        } else {
-          double a = 0.0;
-          for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.wh[j];
-          const double vw = block_sum(a, sm.sc->red);
-          move = (1.0 - wv.kappa) * res.t_plus;
-          for (int j = tid; j < n; j += SPG_THREADS) {
-            sm.p[j] += move * sm.v[j];
-            sm.v[j] -= 2.0 * vw * sm.wh[j];
-          }
-          ell -= res.t_plus;
-          ++nrefl;
-          if (tid == 0) st[kStatReflections] += 1;
-          if (nrefl > wv.rho) {
-            status = kRho;
-          }
-        }
-      } else if (status == kOk) {
-        move = ell;
-        for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += ell * sm.v[j];
-        step_done = true;
-      }
-    } else {
-      if (status == kOk && !(isfinite(res.t_plus) && isfinite(res.t_minus))) status = kUnbounded;
-      if (status == kOk) {
-        const double eta = rng_uniform(wv.seed, chain, wv.step0 + wv.done[c], kStreamEta);
-        move = res.t_minus + eta * (res.t_plus - res.t_minus);
-        for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] += move * sm.v[j];
-        step_done = true;
-      }
-    }
-    __syncthreads();
-    long long tu0 = clock64();
-    if (status != kOk) {
-      // the step is rejected: back to its start point; F(x) is re-formed
-      rejected = true;
-      step_done = true;
-      for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] = wv.Xstart[(size_t)c * n + j];
-      __syncthreads();
-      for (long long e = tid; e < P; e += SPG_THREADS) {
-        const double* Ae = sp.A + e;
-        double f = Ae[0];
-        for (int j = 0; j < n; ++j) f += sm.p[j] * Ae[(size_t)(j + 1) * P];
-        Fc[e] = f;
-      }
+    const bool reflect = wv.kind == 0 && res.status == kOk && res.t_plus < ell;
+    if (wv.pend) {
+      // the wave's normals come from the tensor-core contraction; the
+      // reflection completes in the finish kernel
+      double* ub = wv.Ubuf + (size_t)r * m;
+      for (int i = tid; i < m; i += SPG_THREADS) ub[i] = reflect ? sm.u[i] : 0.0;
       if (tid == 0) {
-        st[kStatBadSteps] += 1;
-        wv.status[c] = status;
+        wv.pend[r] = reflect ? 1 : 0;
+        wv.Tbuf[r] = res.t_plus;
       }
-    } else if (move != 0.0) {
-      // carried F: F(p + move v) = F(p) + move V
-      for (long long e = tid; e < P; e += SPG_THREADS) Fc[e] += move * Vr[e];
+      __syncthreads();
+      if (reflect) continue;
+    } else if (reflect) {
+      long long tc0 = clock64();
+      contract_forms(sp, mw.Ahl, sm);
+      stage_mark(mw, 5, tc0);  // normal contraction
+    }
+    complete_segment(sp, mw, wv, sm, r, c, res.status, res.t_plus, res.t_minus, ell, nrefl, Fc,
+                     Vr, st);
+    __syncthreads();
+  }
+}
+
+// Finish of the deferred reflections of a wave: w_j from the contraction's
+// partial sums (fixed order), then the reflection and the rest of the
+// segment (complete_segment).  One block per pending slot.
+__global__ void __launch_bounds__(SPG_THREADS)
+    mixed_reflect_kernel(DevSpec sp, MixWork mw, MixWave wv, int count) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n;
+  const long long P = sp.P;
+  MixSmem sm;
+  double* d = reinterpret_cast<double*>(smem_raw);
+  sm.p = d; d += n;
+  sm.v = d; d += n;
+  sm.w = d; d += n + 1;
+  sm.wh = d; d += n;
+  sm.bc = d; d += 16;
+  sm.sc = reinterpret_cast<LanczosScalars*>(d);
+  sm.ib = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(sm.sc) + sizeof(LanczosScalars));
+  mw.prof = nullptr;
+  for (int r = blockIdx.x; r < count; r += gridDim.x) {
+    if (!wv.pend[r]) continue;
+    const int c = wv.id_cur[r];
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      sm.p[j] = wv.X[(size_t)c * n + j];
+      sm.v[j] = wv.dir_cur[(size_t)r * n + j];
+    }
+    for (int j = tid; j <= n; j += SPG_THREADS) {
+      const double* wp = wv.Wpart + ((size_t)r * (n + 1) + j) * wv.wtiles;
+      double a = 0.0;
+      for (int t = 0; t < wv.wtiles; ++t) a += wp[t];
+      sm.w[j] = a;
     }
     __syncthreads();
-    int done = wv.done[c];
-    if (step_done) {
-      ++done;
-      nrefl = 0;
-      ell = 0.0;
-      for (int j = tid; j < n; j += SPG_THREADS) wv.Xstart[(size_t)c * n + j] = sm.p[j];
-      if (done < wv.steps) {
-        const uint32_t stp = wv.step0 + (uint32_t)done;
-        if (wv.kind == 2) {
-          const double uc = rng_uniform(wv.seed, chain, stp, kStreamCoord);
-          int jc = (int)(uc * n);
-          jc = jc < n ? jc : n - 1;
-          for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = (j == jc) ? 1.0 : 0.0;
-          __syncthreads();
-        } else {
-          draw_direction(wv.seed, chain, stp, sm.v, n, sm);
-        }
-        if (wv.kind == 0) ell = -wv.tau * log(rng_uniform(wv.seed, chain, stp, kStreamEta));
-      }
-    }
-    for (int j = tid; j < n; j += SPG_THREADS) wv.X[(size_t)c * n + j] = sm.p[j];
-    if (done < wv.steps) {
-      // still active: queue the chain (and its direction) for the next wave
-      if (tid == 0) sm.ib[1] = atomicAdd(wv.count_next, 1);
-      __syncthreads();
-      const int slot = sm.ib[1];
-      for (int j = tid; j < n; j += SPG_THREADS) wv.dir_next[(size_t)slot * n + j] = sm.v[j];
-      if (tid == 0) wv.id_next[slot] = c;
-    }
-    stage_mark(mw, 6, tu0);  // F update, next direction, queueing
-    if (tid == 0) {
-      wv.done[c] = done;
-      wv.ell[c] = ell;
-      wv.nrefl[c] = nrefl;
-      wv.tprev[c] = (rejected || step_done) ? 0.0 : res.t_plus;
-    }
+    complete_segment(sp, mw, wv, sm, r, c, kOk, wv.Tbuf[r], -INFINITY, wv.ell[c], wv.nrefl[c],
+                     wv.F + (size_t)c * P, wv.Vrows + (size_t)r * P,
+                     wv.stats + (size_t)c * kNumStats);
     __syncthreads();
   }
 }
@@ -988,6 +1060,14 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       }
       if (pp.u && status == kOk)
         for (int i = tid; i < m; i += SPG_THREADS) pp.u[(size_t)c * m + i] = sm.u[i];
+    } else if (pp.Ubuf) {
+      // normals of all lines at once on the tensor cores (finish kernel)
+      for (int i = tid; i < m; i += SPG_THREADS)
+        pp.Ubuf[(size_t)c * m + i] = status == kOk ? sm.u[i] : 0.0;
+      if (tid == 0) {
+        pp.t_plus[c] = res.t_plus;
+        pp.status[c] = status == kOk ? res.status : status;
+      }
     } else {
       if (status == kOk) {
         contract_forms(sp, mw.Ahl, sm);
@@ -1006,6 +1086,45 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       if (tid == 0) {
         pp.t_plus[c] = res.t_plus;
         pp.status[c] = status == kOk ? res.status : status;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// reflect, second half: w_j from the contraction's partial sums, unit normal
+// and reflected direction (Eq. "reflection") for every line whose oracle
+// call succeeded
+__global__ void __launch_bounds__(SPG_THREADS) prim_reflect_finish_kernel(DevSpec sp, PrimParams pp) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int tid = threadIdx.x;
+  const int n = sp.n;
+  MixSmem sm;
+  double* d = reinterpret_cast<double*>(smem_raw);
+  sm.w = d; d += n + 1;
+  sm.wh = d; d += n;
+  sm.sc = reinterpret_cast<LanczosScalars*>(d);
+  for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
+    const int st0 = pp.status[c];
+    if (!(st0 == kOk || st0 == kNoConv)) continue;
+    for (int j = tid; j <= n; j += SPG_THREADS) {
+      const double* wp = pp.Wpart + ((size_t)c * (n + 1) + j) * pp.wtiles;
+      double a = 0.0;
+      for (int t = 0; t < pp.wtiles; ++t) a += wp[t];
+      sm.w[j] = a;
+    }
+    __syncthreads();
+    const double nw = mix_unit_normal(sm, n);
+    if (!(nw > 0.0)) {
+      if (tid == 0) pp.status[c] = kDegenerate;
+    } else {
+      const double* v = pp.v + (size_t)c * n;
+      double a = 0.0;
+      for (int j = tid; j < n; j += SPG_THREADS) a += v[j] * sm.wh[j];
+      const double vw = block_sum(a, sm.sc->red);
+      for (int j = tid; j < n; j += SPG_THREADS) {
+        pp.w_hat[(size_t)c * n + j] = sm.wh[j];
+        pp.s[(size_t)c * n + j] = v[j] - 2.0 * vw * sm.wh[j];
       }
     }
     __syncthreads();
@@ -1062,6 +1181,25 @@ cudaError_t launch_mixed_wave(const DevSpec& sp, const MixWork& mw, const MixWav
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   mixed_wave_kernel<<<mw.ctas, SPG_THREADS, smem, st>>>(sp, mw, wv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_reflect_finish(const DevSpec& sp, const PrimParams& pp, int ctas,
+                                       cudaStream_t st) {
+  if (pp.count <= 0) return cudaSuccess;
+  const size_t smem = 8 * ((size_t)2 * sp.n + 1) + sizeof(LanczosScalars);
+  const int grid = pp.count < ctas ? pp.count : ctas;
+  prim_reflect_finish_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, pp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_reflect(const DevSpec& sp, const MixWave& wv, int count, int ctas,
+                                 cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = 8 * ((size_t)4 * sp.n + 1 + 16) + sizeof(LanczosScalars) + 16 * sizeof(int);
+  MixWork mw{};
+  const int grid = count < ctas ? count : ctas;
+  mixed_reflect_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, mw, wv, count);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ def _bind(L):
     f("sp_mlp_forward", [_vp, _i, _vp, _vp, _vp])
     f("sp_mlp_gradients", [_vp, _i, _vp, _vp, _vp, _vp, _vp])
     f("sp_mlp_train", [_vp, _i, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp])
+    f("sp_mlp_save", [_vp, ctypes.c_char_p])
+    f("sp_mlp_load", [ctypes.c_char_p, ctypes.c_uint64, ctypes.POINTER(_vp)])
 
 
 def lib():
@@ -312,10 +314,11 @@ class Chains:
 
     def kernel_timing(self, enable: int = -1):
         """Per-kernel CUDA-event timing of walk calls (see sp_kernel_timing)."""
-        out = (ctypes.c_double * 9)()
+        out = (ctypes.c_double * 13)()
         _check(lib().sp_kernel_timing(self._h, enable, out))
         k = ["fp64_ms", "fp64_launches", "form_ms", "form_launches", "wave_ms", "wave_launches",
-             "mlp_ms", "mlp_launches", "other_launches"]
+             "mlp_ms", "mlp_launches", "other_launches", "contract_ms", "contract_launches",
+             "finish_ms", "finish_launches"]
         return {name: out[i] for i, name in enumerate(k)}
 
     def record(self, x_out=None, y_out=None, count=None):
@@ -350,6 +353,24 @@ class MLP:
         npar = ctypes.c_longlong(0)
         _check(lib().sp_mlp_dims(h, None, None, None, ctypes.byref(npar)))
         self.nparams = npar.value
+
+    @classmethod
+    def load(cls, path: str, seed: int = 0) -> "MLP":
+        """A network saved by save() (sp_mlp_load)."""
+        h = _vp()
+        _check(lib().sp_mlp_load(os.fsencode(path), seed, ctypes.byref(h)))
+        q = cls.__new__(cls)
+        q._h = h
+        din, dh, dout = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        npar = ctypes.c_longlong(0)
+        _check(lib().sp_mlp_dims(h, ctypes.byref(din), ctypes.byref(dh), ctypes.byref(dout),
+                                 ctypes.byref(npar)))
+        q.din, q.dh, q.dout, q.nparams = din.value, dh.value, dout.value, npar.value
+        return q
+
+    def save(self, path: str) -> None:
+        """Write the network to a file (sp_mlp_save)."""
+        _check(lib().sp_mlp_save(self._h, os.fsencode(path)))
 
     @property
     def handle(self):

@@ -89,3 +89,20 @@ def test_training_reduces_the_loss(spectra):
     losses = net.train(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), epochs=60,
                        batch=256, lr=2e-3)
     assert losses[-1] < 0.3 * losses[0], losses
+
+
+def test_save_and_load_round_trip(spectra, tmp_path):
+    """sp_mlp_save / sp_mlp_load keep the dimensions, the parameters bit for
+    bit and hence the forward pass."""
+    net = spectra.MLP(20, 64, 22, seed=5)
+    path = str(tmp_path / "net.spmlp")
+    net.save(path)
+    other = spectra.MLP.load(path)
+    assert (other.din, other.dh, other.dout) == (20, 64, 22)
+    assert np.array_equal(other.params(), net.params())
+    X = torch.randn(64, 20, dtype=torch.float32, device="cuda")
+    assert torch.equal(net.forward(X), other.forward(X))
+    with open(path, "r+b") as f:  # a corrupted header is rejected
+        f.write(b"XXXX")
+    with pytest.raises(spectra.SpectraError):
+        spectra.MLP.load(path)
