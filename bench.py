@@ -5,13 +5,16 @@ A bench "step" is one Billiard step (Alg. 5) of every chain: each chain draws
 a direction and a length and runs the boundary oracle (pencil, Cholesky,
 extreme eigenpair, normal, reflection) until the length is used up.
 
-The headline path (--mode, default "learned") is timed for --steps steps after
---warmup steps; the two other paths ("fp64": every step in FP64; "mixed":
-tensor-core formation, FP32 estimate, FP64 factorisation next to the boundary)
-are timed on the same workload for context (2 steps after 1 warm-up each).
-The learned path first trains its warm-start network on tuples recorded from
-a mixed-precision walk (outside the timed region).  Every path's t+ and
-normal are checked against the FP64 CPU oracle on sampled walk states.
+First --burn-in mixed-precision steps take the chains from their start cloud
+into the body (recording the learned path's training tuples on the way) and
+the warm-start network is trained on the GPU; all of this is outside the
+timed region.  Then every path starts from that same state and is timed for
+--steps steps after --warmup steps (the same step window for all): the
+headline path (--mode, default "learned") and, for context, the others
+("fp64": every step in FP64; "mixed": tensor-core formation and normals,
+FP32 estimate, double-float refinement next to the boundary).  Every path's
+t+ and normal are checked against the FP64 CPU oracle on sampled walk
+states.
 
 Chains are independent, so N GPUs run N replicas on disjoint chain ranges
 (weak scaling, no collective on the data path).  Prints one JSON line (rank
@@ -49,8 +52,11 @@ WORKLOAD = "Dabbene S-200-200 (n=m=200), 8192 chains, Billiard walk"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--burn-in", type=int, default=4,
+                   help="mixed Billiard steps from the start cloud before any path is timed; "
+                        "every path then starts from that state (the same step window)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="learned", choices=["fp64", "mixed", "learned"])
     p.add_argument("--only", action="store_true", help="time the --mode path alone")
@@ -63,7 +69,7 @@ def parse():
     p.add_argument("--tau-scale", type=float, default=1.0,
                    help="scale tau (a small value gives short steps, for profiling captures)")
     p.add_argument("--train-tuples", type=int, default=262144)
-    p.add_argument("--train-epochs", type=int, default=8)
+    p.add_argument("--train-epochs", type=int, default=24)
     return p.parse_args()
 
 
@@ -238,8 +244,24 @@ def _peaks():
 # ----------------------------------------------------------------------------
 # the walk on one path
 # ----------------------------------------------------------------------------
-def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, stage_timers=False):
+def burn_in(spectra, torch, spec, C, rank, steps, tau, record=None):
+    """Mixed Billiard steps from the start cloud (recording training tuples
+    when `record` = (X, Y, counter)); returns the host state (x, step)."""
     chains = spectra.Chains(spec, C, x0=start_points(C, rank), seed=SEED_WALK, chain0=rank * C)
+    if record is not None:
+        chains.record(*record)
+    for _ in range(steps):
+        chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode="mixed")
+    if record is not None:
+        chains.record()
+    torch.cuda.synchronize()
+    return chains.state_host()
+
+
+def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, state,
+              stage_timers=False):
+    chains = spectra.Chains(spec, C, x0=start_points(C, rank), seed=SEED_WALK, chain0=rank * C)
+    chains.set_state(state[0], state[1])
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=mode)
@@ -304,24 +326,13 @@ def oracle_check(spectra, torch, spec, A, chains, mode, samples):
             "status_ok": bool((st == 0).all())}
 
 
-def train_network(spectra, torch, spec, C, epochs, tuples):
-    """Record (x, v) -> (log t+, u) tuples from a mixed-precision walk on the
-    same spectrahedron (other seed) and train the network on the GPU."""
-    t0 = time.perf_counter()
+def train_network(spectra, torch, spec, X, Y, cnt, epochs, record_s, walk_steps):
+    """Train the warm-start network on the GPU on the (x, v) -> (log t+, u)
+    tuples that the mixed walk recorded on the same spectrahedron."""
     net = spectra.MLP(2 * N_DIM, 512, 1 + M_DIM, seed=SEED_TRAIN)
     spec.attach_mlp(net, x_scale=1.0 / TAU, t_scale=T_SCALE, margin=0.05, iters=12)
-    X = torch.zeros((tuples, 2 * N_DIM), dtype=torch.float32, device="cuda")
-    Y = torch.zeros((tuples, 1 + M_DIM), dtype=torch.float32, device="cuda")
-    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ch = spectra.Chains(spec, C, x0=start_points(C, 99), seed=SEED_TRAIN)
-    ch.record(X, Y, cnt)
-    walk_steps = 0
-    while int(cnt.item()) < tuples and walk_steps < 64:
-        ch.billiard(1, tau=TAU, rho=RHO, kappa=KAPPA, mode="mixed")
-        walk_steps += 1
-    ch.record()
-    got = min(int(cnt.item()), tuples)
-    t1 = time.perf_counter()
+    got = min(int(cnt.item()), X.shape[0])
+    t0 = t1 = time.perf_counter()
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     perm = torch.randperm(got, device="cuda", generator=g)
@@ -335,7 +346,7 @@ def train_network(spectra, torch, spec, C, epochs, tuples):
     lt_err = (Yp[:, 0] - Y[:nval, 0]).abs()
     cos = ((Yp[:, 1:] * Y[:nval, 1:]).sum(1).abs()
            / (Yp[:, 1:].norm(dim=1) * Y[:nval, 1:].norm(dim=1)))
-    return net, {"tuples": got, "walk_steps": walk_steps, "record_s": t1 - t0,
+    return net, {"tuples": got, "walk_steps": walk_steps, "record_s": record_s,
                  "train_s": t2 - t1, "epochs": epochs, "final_loss": float(losses[-1]),
                  "val_rel_err_t_median": float(torch.expm1(lt_err).median()),
                  "val_rel_err_t_p90": float(torch.expm1(lt_err).quantile(0.9)),
@@ -366,23 +377,36 @@ def main():
     tau = TAU * args.tau_scale
     C = args.chains
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # burn-in (mixed walk from the start cloud; it records the training tuples
+    # of the learned path), then the network's training on the GPU
+    learned = args.mode == "learned" or not args.only
+    record = None
+    if learned:
+        record = (torch.zeros((args.train_tuples, 2 * N_DIM), dtype=torch.float32, device="cuda"),
+                  torch.zeros((args.train_tuples, 1 + M_DIM), dtype=torch.float32, device="cuda"),
+                  torch.zeros(1, dtype=torch.int32, device="cuda"))
+    t0 = time.perf_counter()
+    state = burn_in(spectra, torch, spec, C, rank, args.burn_in, tau, record)
+    burn_s = time.perf_counter() - t0
     train_info = None
-    if args.mode == "learned":
-        _net, train_info = train_network(spectra, torch, spec, min(C, 8192), args.train_epochs,
-                                         args.train_tuples)
+    if learned:
+        _net, train_info = train_network(spectra, torch, spec, *record, args.train_epochs,
+                                         burn_s, args.burn_in)
 
-    # context paths first (short), then the headline path under the clock sampler
+    # every path from the same state over the same step window: context paths
+    # first, then the headline path under the clock sampler
     context = {}
     if not args.only:
         for mode in ["fp64", "mixed", "learned"]:
-            if mode == args.mode or (mode == "learned" and train_info is None):
+            if mode == args.mode:
                 continue
-            context[mode] = time_path(spectra, torch, spec, mode, C, rank, 2, 1, tau, flush)
+            context[mode] = time_path(spectra, torch, spec, mode, C, rank, args.steps,
+                                      args.warmup, tau, flush, state)
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
         head = time_path(spectra, torch, spec, args.mode, C, rank, args.steps, args.warmup, tau,
-                         flush, stage_timers=args.stage_timers)
+                         flush, state, stage_timers=args.stage_timers)
     if world > 1:
         dist.barrier()
     t_max = head["dev_ms"]

@@ -88,9 +88,11 @@ const char* sp_version(void);
  *           A_i must be symmetric (checked to 1e-12 relative; SP_EINVAL
  *           otherwise).  The library copies and packs it (lower triangles) to
  *           device memory; the caller keeps ownership of A.
- *   flags : reserved, pass 0.
+ *   flags : bit 0 (SP_FLAG_FP64_ONLY): skip the mixed path's precomputed
+ *           operands (digit stacks, FP32 pairs); other bits reserved, 0.
  *   out   : receives the handle; free with sp_destroy_spectrahedron.
  */
+#define SP_FLAG_FP64_ONLY 1u
 int sp_create_spectrahedron(int n, int m, const double* A, uint32_t flags, sp_spec** out);
 int sp_destroy_spectrahedron(sp_spec* s);
 int sp_spec_dims(const sp_spec* s, int* n, int* m);
@@ -166,6 +168,32 @@ int sp_step_hnr(sp_chains* ch, int steps, int mode, void* stream);
 
 /* Coordinate-direction Hit-and-Run (Sec. 3.1, CDHR): direction e_j, j uniform. */
 int sp_step_cdhr(sp_chains* ch, int steps, int mode, void* stream);
+
+/*
+ * Volume of S by multiphase Monte Carlo over a sequence of balls (Sec. 4.1,
+ * the multiphase scheme with the Billiard walk): radii r_0 = r_inner < r_1 <
+ * ... < r_q = r_outer, geometric, q = ceil(n ln(r_outer / r_inner) / ln(1 /
+ * ratio)) so that each ratio vol(S cap B(r_{i-1})) / vol(S cap B(r_i)) is
+ * about `ratio` for a body that fills its balls; then
+ *   vol(S) = vol(B(r_0)) prod_i 1 / f_i,
+ * f_i the fraction of samples of S cap B(r_i) in B(r_{i-1}).  Each phase
+ * creates the spectrahedron S cap B(r_i) (the ball block [[r_i, x^T],
+ * [x, r_i I_n]] appended to the LMI), starts `chains` chains at the origin
+ * (seed + i), runs `burn_in` steps and then `steps` steps, counting every
+ * chain's point after every step.  walk: 0 Billiard (tau = 2 r_i, rho =
+ * 1000, kappa = 1e-6), 1 Hit-and-Run; mode: SP_MODE_FP64 or SP_MODE_MIXED.
+ * Requires the origin interior to S, B(r_inner) inside S and S inside
+ * B(r_outer) (otherwise the result is the volume of S cap B(r_outer) times
+ * vol(B(r_inner)) / vol(S cap B(r_inner))).  vol (host): the estimate; info
+ * (host, 4 doubles, may be NULL): phases q, samples per phase, relative
+ * standard error from the per-phase binomial errors (the chains'
+ * autocorrelation is ignored, so it is optimistic), wall seconds.
+ * Synchronises `stream`.  SP_EINVAL for bad arguments or a phase with no
+ * sample in the smaller ball.
+ */
+int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio, int chains,
+                       int burn_in, int steps, int walk, int mode, uint64_t seed, double* vol,
+                       double* info, void* stream);
 
 /*
  * Chain state.

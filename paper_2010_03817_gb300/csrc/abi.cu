@@ -295,6 +295,16 @@ struct sp_chains {
   }
 };
 
+namespace spg {
+int spec_copy_stack(const sp_spec* s, double* packed_host) {
+  const size_t bytes = sizeof(double) * (size_t)(s->n + 1) * s->P;
+  if (cudaMemcpy(packed_host, s->A, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "LMI stack copy");
+  return SP_OK;
+}
+const double* chain_points(const sp_chains* ch) { return ch->X; }
+}  // namespace spg
+
 extern "C" {
 
 const char* sp_last_error(void) { return g_err.c_str(); }

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
   bool ok = true;
   for (int kt = 0; kt < KT; ++kt) {
     const int buf = kt & 1;
-    if (kt >= 2 && !tc::mbar_wait(&mbar[buf], ((kt - 2) >> 1) & 1)) {
+    const bool w = kt < 2 || tc::mbar_wait(&mbar[buf], ((kt - 2) >> 1) & 1);
+    if (!__syncthreads_and(w)) {  // a block-uniform verdict
       ok = false;
       break;
     }
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
   }
   if (ok && KT > 0) ok = tc::mbar_wait(&mbar[(KT - 1) & 1], ((KT - 1) >> 1) & 1);
+  ok = __syncthreads_and(ok);  // the epilogue's TMEM loads are warp-collective
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
     if (KT > 0) tc::mbar_wait(&mbar[(KT - 1) & 1], ((KT - 1) >> 1) & 1, 1ll << 20);

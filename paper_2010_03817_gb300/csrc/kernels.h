@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct sp_spec;
+struct sp_chains;
+
 struct sp_mlp;
 // forward pass of the warm-start network on B rows of device features X;
 // *Y receives the device output (B rows, leading dimension *ld)
@@ -202,5 +205,11 @@ cudaError_t launch_walk_fp64(const DevSpec& sp, const DevWork& wk, const WalkPar
                              cudaStream_t st);
 cudaError_t launch_prim_fp64(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
                              cudaStream_t st);
+
+// library internals for the host drivers (abi.cu): the packed LMI stack
+// ((n+1) x P doubles) copied to the host, and the device array of a chain
+// set's points (C x n)
+int spec_copy_stack(const sp_spec* s, double* packed_host);
+const double* chain_points(const sp_chains* ch);
 
 }  // namespace spg

@@ -150,17 +150,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tmem_alloc(tmem_slot, 256);
     tc::tmem_relinquish();
   }
-  // B digits of this column tile (all of them stay resident)
-  for (int t = 0; t < kDigits; ++t) {
-    uint8_t* dst = sB + t * b_bytes;
+  // All operand tiles arrive by 16-byte asynchronous copies, many in flight
+  // per thread: the 7 B digit planes of this column tile (resident) and A
+  // digit plane 0 first; plane s + 1 streams into the other buffer while the
+  // tensor core works on plane s.
+  const uint32_t sB_u = tc::smem_u32(sB), sA_u[2] = {tc::smem_u32(sA0), tc::smem_u32(sA1)};
+  for (int t = 0; t < kDigits; ++t)
     for (int q = tid; q < kTileN * kgroups; q += kThreads) {
       const int r = q / kgroups, g = q % kgroups;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (p0 + r < P)
-        v = *reinterpret_cast<const uint4*>(Bsl + ((size_t)t * P + p0 + r) * Kp + g * 8);
-      *reinterpret_cast<uint4*>(dst + core_off(r, g, kgroups)) = v;
+      const bool in = p0 + r < P;
+      tc::cp_async16(sB_u + t * b_bytes + core_off(r, g, kgroups),
+                     in ? Bsl + ((size_t)t * P + p0 + r) * Kp + g * 8 : Bsl, in);
     }
-  }
+  tc::cp_async_commit();
+  auto stage_a = [&](int s) {
+    const uint32_t base = sA_u[s & 1];
+    for (int q = tid; q < kTileM * kgroups; q += kThreads) {
+      const int r = q / kgroups, g = q % kgroups;
+      const bool in = r0 + r < R;
+      tc::cp_async16(base + core_off(r, g, kgroups),
+                     in ? Asl + ((size_t)s * R + r0 + r) * Kp + g * 8 : Asl, in);
+    }
+    tc::cp_async_commit();
+  };
+  stage_a(0);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -170,26 +183,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool ok = true;
 
   for (int s = 0; s < kDigits; ++s) {
-    const int buf = s & 1;
-    uint8_t* sA = buf ? sA1 : sA0;
-    if (s >= 2 && !tc::mbar_wait(&mbar[buf], ((s - 2) >> 1) & 1)) {
-      ok = false;
-      break;
-    }
-    for (int q = tid; q < kTileM * kgroups; q += kThreads) {
-      const int r = q / kgroups, g = q % kgroups;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (r0 + r < R)
-        v = *reinterpret_cast<const uint4*>(Asl + ((size_t)s * R + r0 + r) * Kp + g * 8);
-      *reinterpret_cast<uint4*>(sA + core_off(r, g, kgroups)) = v;
+    if (s + 1 < kDigits) {
+      // buffer (s + 1) & 1 was last read by the MMAs of plane s - 1; the
+      // verdict of the bounded wait is made block-uniform
+      const bool w = s < 1 || tc::mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1);
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+      stage_a(s + 1);
+      tc::cp_async_wait<1>();  // everything but plane s + 1 has landed
+    } else {
+      tc::cp_async_wait<0>();
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t a_base = tc::smem_u32(sA);
+      const uint32_t a_base = sA_u[s & 1];
       for (int t = 0; t + s < kGroups; ++t) {
-        const uint32_t b_base = tc::smem_u32(sB + t * b_bytes);
+        const uint32_t b_base = sB_u + t * b_bytes;
         const uint32_t d_tmem = tmem + (uint32_t)((s + t) * kTileN);
         for (int ks = 0; ks < Kp / 16; ++ks) {
           const uint64_t ad = tc::smem_desc(a_base + ks * 256, 128, sbo);
@@ -197,11 +210,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::mma_bf16(d_tmem, ad, bd, idesc, (s > 0 || ks > 0) ? 1u : 0u);
         }
       }
-      tc::mma_commit(&mbar[buf]);
+      tc::mma_commit(&mbar[s & 1]);
     }
   }
+  tc::cp_async_wait<0>();  // no copy may still be in flight when the block moves on
   // the commit of the last digit covers every MMA issued before it
   if (ok) ok = tc::mbar_wait(&mbar[(kDigits - 1) & 1], ((kDigits - 1) >> 1) & 1);
+  ok = __syncthreads_and(ok);  // the epilogue's TMEM loads are warp-collective
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
     // let in-flight MMAs drain (bounded) before the TMEM is released

@@ -108,6 +108,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
 }
 
 // ---- TMEM -> registers: 32 lanes x 32 bit, 16 consecutive columns ---------
+// 16-byte asynchronous copy global -> shared (L2 only); src_bytes 0 writes
+// zeros (the source is not read)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// wait until at most N groups committed by this thread are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "

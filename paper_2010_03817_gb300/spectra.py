@@ -49,6 +49,8 @@ def _bind(L):
     f("sp_spec_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
     f("sp_set_solver", [_vp, _i, _d, _d])
     f("sp_membership", [_vp, _i, _vp, _vp, _vp])
+    f("sp_volume_estimate", [_vp, _d, _d, _d, _i, _i, _i, _i, _i, ctypes.c_uint64, _vp, _vp,
+                             _vp])
     f("sp_intersect", [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp])
     f("sp_reflect", [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp])
     f("sp_init_chains", [_vp, _i, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_vp),
@@ -202,6 +204,19 @@ class Spectrahedron:
             _dev(F) if F is not None else None, _dev(V) if V is not None else None, MODES[mode],
             _stream(stream)))
         return F, V
+
+    def volume(self, r_inner: float, r_outer: float, ratio: float = 0.5, chains: int = 4096,
+               burn_in: int = 10, steps: int = 20, walk: str = "billiard", mode: str = "fp64",
+               seed: int = 1, stream=None):
+        """Multiphase Monte Carlo volume over a sequence of balls (sp_volume_estimate):
+        (volume, {"phases", "samples_per_phase", "rel_std_err", "seconds"})."""
+        vol = ctypes.c_double(0.0)
+        info = (ctypes.c_double * 4)()
+        _check(lib().sp_volume_estimate(self._h, r_inner, r_outer, ratio, chains, burn_in, steps,
+                                        {"billiard": 0, "hnr": 1}[walk], MODES[mode], seed,
+                                        ctypes.byref(vol), info, _stream(stream)))
+        return vol.value, {"phases": int(info[0]), "samples_per_phase": int(info[1]),
+                           "rel_std_err": info[2], "seconds": info[3]}
 
     def membership(self, x, stream=None):
         import torch
