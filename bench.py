@@ -68,6 +68,8 @@ def parse():
                    help="report the mixed path's per-stage cycle shares")
     p.add_argument("--tau-scale", type=float, default=1.0,
                    help="scale tau (a small value gives short steps, for profiling captures)")
+    p.add_argument("--tol32", type=float, default=None,
+                   help="stage-1 FP32 Lanczos tolerance of the mixed paths (library default 1e-5)")
     p.add_argument("--train-tuples", type=int, default=262144)
     p.add_argument("--train-epochs", type=int, default=24)
     return p.parse_args()
@@ -374,6 +376,8 @@ def main():
     spectra.lib()
     A = workload()
     spec = spectra.Spectrahedron(A)
+    if args.tol32 is not None:
+        spec.set_mixed_solver(tol32=args.tol32)
     tau = TAU * args.tau_scale
     C = args.chains
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

@@ -441,6 +441,20 @@ int sp_set_solver(sp_spec* s, int kmax, double tol, double sigma_frac) {
   return SP_OK;
 }
 
+int sp_set_mixed_solver(sp_spec* s, double tol32, double tol64, double delta1, int power_iters) {
+  if (!s) return fail(SP_EINVAL, "sp_set_mixed_solver: null handle%s");
+  if (!(tol32 > 0.0 && tol32 < 1.0) || !(tol64 > 0.0 && tol64 < 1.0) ||
+      !(delta1 > 0.0 && delta1 < 0.5) || power_iters < 1 || power_iters > 64)
+    return fail(SP_EINVAL,
+                "sp_set_mixed_solver: tol32, tol64 in (0,1), delta1 in (0,0.5), power_iters in "
+                "[1,64]%s");
+  s->tol32 = tol32;
+  s->tol64 = tol64;
+  s->delta1 = delta1;
+  s->power_iters = power_iters;
+  return SP_OK;
+}
+
 static int check_mode(int mode, const char* fn) {
   if (mode != SP_MODE_FP64 && mode != SP_MODE_MIXED && mode != SP_MODE_LEARNED)
     return fail(SP_EINVAL, "%s: unknown mode", fn);

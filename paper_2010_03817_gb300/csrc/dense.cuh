@@ -33,6 +33,13 @@ __device__ __forceinline__ double recip_t(double x) {
   return r;
 }
 
+// acc += a b; the double-float type overloads it with a cheaper form that
+// leaves the renormalisation to the end of the accumulation
+template <typename T>
+__device__ __forceinline__ void mac_acc(T& acc, T a, T b) {
+  acc += a * b;
+}
+
 // In-place Cholesky G = L L^T of the packed lower triangle G (m x m),
 // right-looking in panels of kPanel = 8 columns, three barriers per panel:
 //   1. warp 0 factors the 8 x 8 diagonal block in registers (lane r holds
@@ -126,10 +133,10 @@ __device__ bool factor_cholesky(T* G, int m, T* pan_raw, int* flag) {
       for (int c = 0; c < kPanel; ++c) g[c] = G[base + c];
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) {
-        T acc = g[c];
+        T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < c; ++k) acc -= g[k] * pan[k * ld + jb + c];
-        g[c] = acc * pan[c * ld + jb + c];
+        for (int k = 0; k < c; ++k) mac_acc(acc, g[k], pan[k * ld + jb + c]);
+        g[c] = (g[c] - acc) * pan[c * ld + jb + c];
       }
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) {
@@ -164,7 +171,7 @@ __device__ bool factor_cholesky(T* G, int m, T* pan_raw, int* flag) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] += va[a] * vb[b];
+          for (int b = 0; b < 4; ++b) mac_acc(acc[a][b], va[a], vb[b]);
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -198,7 +205,7 @@ __device__ void invert_diag_blocks(T* L, int m) {
       const T rdrr = recip_t(L[tri(r0 + r, r0 + r)]);
       if (lane < r) {
         T acc = T(0);
-        for (int k = lane; k < r; ++k) acc += L[tri(r0 + r, r0 + k)] * L[tri(r0 + k, r0 + lane)];
+        for (int k = lane; k < r; ++k) mac_acc(acc, L[tri(r0 + r, r0 + k)], L[tri(r0 + k, r0 + lane)]);
         val = -acc * rdrr;
       } else if (lane == r) {
         val = rdrr;
@@ -231,7 +238,7 @@ __device__ void solve_lower(const T* L, T* x, int m, T* s) {
 #pragma unroll
         for (int q = 0; q < kRows; ++q) {
           const int rr = wid + SPG_WARPS * q;
-          if (rr < bs) acc[q] += L[tri(r0 + rr, k)] * xk;
+          if (rr < bs) mac_acc(acc[q], L[tri(r0 + rr, k)], xk);
         }
       }
 #pragma unroll
@@ -251,12 +258,12 @@ __device__ void solve_lower(const T* L, T* x, int m, T* s) {
       T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
       int c = 0;
       for (; c + 3 <= lane; c += 4) {
-        a0 += row[c] * s[c];
-        a1 += row[c + 1] * s[c + 1];
-        a2 += row[c + 2] * s[c + 2];
-        a3 += row[c + 3] * s[c + 3];
+        mac_acc(a0, row[c], s[c]);
+        mac_acc(a1, row[c + 1], s[c + 1]);
+        mac_acc(a2, row[c + 2], s[c + 2]);
+        mac_acc(a3, row[c + 3], s[c + 3]);
       }
-      for (; c <= lane; ++c) a0 += row[c] * s[c];
+      for (; c <= lane; ++c) mac_acc(a0, row[c], s[c]);
       x[r0 + lane] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
@@ -279,10 +286,10 @@ __device__ void solve_upper(const T* L, T* x, int m, T* s) {
     if (lane < bs) {
       int r = r0 + bs + wid;
       for (; r + SPG_WARPS < m; r += 2 * SPG_WARPS) {
-        acc += L[tri(r, i)] * x[r];
-        acc2 += L[tri(r + SPG_WARPS, i)] * x[r + SPG_WARPS];
+        mac_acc(acc, L[tri(r, i)], x[r]);
+        mac_acc(acc2, L[tri(r + SPG_WARPS, i)], x[r + SPG_WARPS]);
       }
-      if (r < m) acc += L[tri(r, i)] * x[r];
+      if (r < m) mac_acc(acc, L[tri(r, i)], x[r]);
     }
     part[wid * kBlk + lane] = acc + acc2;
     __syncthreads();
@@ -298,12 +305,12 @@ __device__ void solve_upper(const T* L, T* x, int m, T* s) {
       T z0 = T(0), z1 = T(0), z2 = T(0), z3 = T(0);
       int rr = lane;
       for (; rr + 3 < bs; rr += 4) {
-        z0 += L[tri(r0 + rr, i)] * s[rr];
-        z1 += L[tri(r0 + rr + 1, i)] * s[rr + 1];
-        z2 += L[tri(r0 + rr + 2, i)] * s[rr + 2];
-        z3 += L[tri(r0 + rr + 3, i)] * s[rr + 3];
+        mac_acc(z0, L[tri(r0 + rr, i)], s[rr]);
+        mac_acc(z1, L[tri(r0 + rr + 1, i)], s[rr + 1]);
+        mac_acc(z2, L[tri(r0 + rr + 2, i)], s[rr + 2]);
+        mac_acc(z3, L[tri(r0 + rr + 3, i)], s[rr + 3]);
       }
-      for (; rr < bs; ++rr) z0 += L[tri(r0 + rr, i)] * s[rr];
+      for (; rr < bs; ++rr) mac_acc(z0, L[tri(r0 + rr, i)], s[rr]);
       x[i] = (z0 + z1) + (z2 + z3);
     }
     __syncthreads();
@@ -350,8 +357,8 @@ __device__ void symv_packed(const S* __restrict__ V, const T* z, T* y, int m, T 
       const int k = lane + 32 * i;
       if (k <= r) {
         const T a = T(row[k]);
-        acc += a * z[k];
-        if (k < r) cacc[i] += a * zr;
+        mac_acc(acc, a, z[k]);
+        if (k < r) mac_acc(cacc[i], a, zr);
       }
     }
     acc = warp_sum(acc);
@@ -386,7 +393,7 @@ __device__ void mul_upper(const T* L, const T* x, T* y, int m, T* part) {
 #pragma unroll
     for (int i = 0; i < kMaxColBlocks; ++i) {
       const int k = lane + 32 * i;
-      if (k <= r) cacc[i] += row[k] * xr;  // (L^T x)_k = sum_{r >= k} L[r][k] x_r
+      if (k <= r) mac_acc(cacc[i], row[k], xr);  // (L^T x)_k = sum_{r >= k} L[r][k] x_r
     }
   }
 #pragma unroll

@@ -158,6 +158,12 @@ __device__ __forceinline__ dfloat rsqrt_t(dfloat x) {
   return r;
 }
 
+// acc += a b without renormalising acc (Dot2-style: the product's error and
+// the sum's error collect in acc.l; the next full operation renormalises)
+__device__ __forceinline__ void mac_acc(dfloat& acc, dfloat a, dfloat b) {
+  df_mac(acc.h, acc.l, a.h, a.l, b.h, b.l);
+}
+
 __device__ __forceinline__ dfloat shfl_idx(dfloat v, int src) {
   return dfloat(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
 }

@@ -482,19 +482,39 @@ __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, 
     }
     __syncthreads();
   }
-  // final Ritz pairs: FP64 inverse iteration at the last estimate (also the
-  // FP64 Rayleigh quotient of T_K)
+  // final Ritz pairs: for an FP64 run, FP64 inverse iteration at the last
+  // estimate, certified extreme by a Sturm count (also the FP64 Rayleigh
+  // quotient of T_K); for an FP32 run, the FP32 analysis
   if (wid == 0) {
-    const double th = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_max, true, sc->s_max,
-                                         sc->cwork);
-    double thn = 0.0;
-    if (want_min)
-      thn = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_min, false, sc->s_min,
-                               sc->cwork);
-    if (lane == 0) {
-      sc->theta_max = th;
-      if (want_min) sc->theta_min = thn;
-      sc->K = K;
+    if (sizeof(T) == 4) {
+      // an FP32 run: the FP32 analysis suffices (the multisection on Sturm
+      // counts returns the extreme eigenvalue itself; a later refinement
+      // certifies the result)
+      const float tmaxf = tri_extreme_f(sc->af, sc->b2f, K, true);
+      const float tminf = want_min ? tri_extreme_f(sc->af, sc->b2f, K, false) : 0.f;
+      if (lane == 0) {
+        float* sfv = sc->sf;
+        float* cwf = sc->sf + kMaxLanczos;
+        sc->theta_max = tri_eigvec_f(sc->af, sc->bf, K, tmaxf, sfv, cwf);
+        for (int j = 0; j < K; ++j) sc->s_max[j] = sfv[j];
+        if (want_min) {
+          sc->theta_min = tri_eigvec_f(sc->af, sc->bf, K, tminf, sfv, cwf);
+          for (int j = 0; j < K; ++j) sc->s_min[j] = sfv[j];
+        }
+        sc->K = K;
+      }
+    } else {
+      const double th = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_max, true,
+                                           sc->s_max, sc->cwork);
+      double thn = 0.0;
+      if (want_min)
+        thn = tri_extreme_pair64(sc->alpha, sc->beta, K, sc->theta_min, false, sc->s_min,
+                                 sc->cwork);
+      if (lane == 0) {
+        sc->theta_max = th;
+        if (want_min) sc->theta_min = thn;
+        sc->K = K;
+      }
     }
   }
   __syncthreads();

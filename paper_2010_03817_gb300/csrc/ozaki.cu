@@ -155,21 +155,38 @@ __global__ void __launch_bounds__(kThreads, 1)
   // digit plane 0 first; plane s + 1 streams into the other buffer while the
   // tensor core works on plane s.
   const uint32_t sB_u = tc::smem_u32(sB), sA_u[2] = {tc::smem_u32(sA0), tc::smem_u32(sA1)};
-  for (int t = 0; t < kDigits; ++t)
+  // (row, 16-byte group) of the copy q = tid + kThreads k, stepped without
+  // divisions: consecutive threads take consecutive groups of a row
+  const int r_init = tid / kgroups, g_init = tid % kgroups;
+  const int dr = kThreads / kgroups, dg = kThreads % kgroups;
+  for (int t = 0; t < kDigits; ++t) {
+    int r = r_init, g = g_init;
     for (int q = tid; q < kTileN * kgroups; q += kThreads) {
-      const int r = q / kgroups, g = q % kgroups;
       const bool in = p0 + r < P;
       tc::cp_async16(sB_u + t * b_bytes + core_off(r, g, kgroups),
                      in ? Bsl + ((size_t)t * P + p0 + r) * Kp + g * 8 : Bsl, in);
+      r += dr;
+      g += dg;
+      if (g >= kgroups) {
+        g -= kgroups;
+        ++r;
+      }
     }
+  }
   tc::cp_async_commit();
   auto stage_a = [&](int s) {
     const uint32_t base = sA_u[s & 1];
+    int r = r_init, g = g_init;
     for (int q = tid; q < kTileM * kgroups; q += kThreads) {
-      const int r = q / kgroups, g = q % kgroups;
       const bool in = r0 + r < R;
       tc::cp_async16(base + core_off(r, g, kgroups),
                      in ? Asl + ((size_t)s * R + r0 + r) * Kp + g * 8 : Asl, in);
+      r += dr;
+      g += dg;
+      if (g >= kgroups) {
+        g -= kgroups;
+        ++r;
+      }
     }
     tc::cp_async_commit();
   };
@@ -231,18 +248,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int jc = kMode == kContract ? (int)(p0 / ep.mpad) : 0;
     const int i0 = kMode == kContract ? (int)(p0 % ep.mpad) : 0;
     for (int c0 = 0; c0 < kTileN; c0 += 16) {
+      // the chunk's exponents and (contraction) u entries or (formation) A_0
+      // entries first: independent loads, in flight together with the TMEM
+      // reads
+      int ec[16];
+      double aux[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const long long p = p0 + c0 + i;
+        ec[i] = p < P ? ecol[p] : 0;
+        if (kMode == kForm) {
+          aux[i] = (ep.lead != 0.0 && p < P) ? ep.A0[p] : 0.0;
+        } else {
+          const int ii = i0 + c0 + i;
+          aux[i] = (r < R && ii < ep.m) ? ep.U[(size_t)r * ep.m + ii] : 0.0;
+        }
+      }
       long long hi[16], lo[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+      uint32_t v[kGroups][16];
+#pragma unroll
+      for (int d = 0; d < kGroups; ++d) tc::tmem_ld16(lane_base + (uint32_t)(d * kTileN + c0), v[d]);
+      tc::tmem_wait_ld();
 #pragma unroll
       for (int d = 0; d < kGroups; ++d) {
-        uint32_t v[16];
-        tc::tmem_ld16(lane_base + (uint32_t)(d * kTileN + c0), v);
-        tc::tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           // exact integers below 2^24 in magnitude
-          const long long g = (long long)__float2int_rn(__uint_as_float(v[i]));
+          const long long g = (long long)__float2int_rn(__uint_as_float(v[d][i]));
           if (d <= 3)
             hi[i] = hi[i] * (1ll << kDigitBits) + g;
           else
@@ -259,20 +293,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const long long p = p0 + c0 + i;
             if (p < P) {
               const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
-                                              er + ecol[p] - 56);
-              yrow[p] = ep.lead != 0.0 ? fma(ep.lead, ep.A0[p], y) : y;
+                                              er + ec[i] - 56);
+              yrow[p] = ep.lead != 0.0 ? fma(ep.lead, aux[i], y) : y;
             }
           }
         } else {
-          const double* ur = ep.U + (size_t)r * ep.m;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int ii = i0 + c0 + i;
-            if (ii < ep.m) {
-              const long long p = p0 + c0 + i;
+            if (i0 + c0 + i < ep.m) {
               const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
-                                              er + ecol[p] - 56);
-              part = fma(y, ur[ii], part);
+                                              er + ec[i] - 56);
+              part = fma(y, aux[i], part);
             }
           }
         }

@@ -83,7 +83,7 @@ struct SegResult {
 };
 
 // One boundary-oracle evaluation for the line p + t v (CTA-wide).
-__device__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
+__device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
                                   double* __restrict__ Vfull, double* __restrict__ Fg,
                                   double* __restrict__ Q, double sigma, bool want_min,
                                   bool want_w, bool form_f) {

@@ -245,7 +245,7 @@ __device__ void symv_df2(const double* __restrict__ F, const double* __restrict_
 // (packed FP64, global) in double-float; stationary at the null vector, so
 // an FP32-accurate u gives t to about FP32 precision squared.  scr: the
 // region after the FP32 factor (4 SPG_WARPS 256 floats).
-__device__ double pencil_rq(const double* Fg, const double* Vg, const double* u, int m,
+__device__ __noinline__ double pencil_rq(const double* Fg, const double* Vg, const double* u, int m,
                             MixSmem& sm, float* scr) {
   for (int i = threadIdx.x; i < m; i += SPG_THREADS) {
     const float2 s = split_df(u[i]);
@@ -276,7 +276,7 @@ __device__ double pencil_rq(const double* Fg, const double* Vg, const double* u,
 //   from y = L^T u0 (u0 slightly perturbed), certificate as in the FP64
 //   refinement.  u0 (FP64) in sm.u, left untouched unless the result is
 //   kOk: then t and the unit null vector (sm.u).
-__device__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+__device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
                              const double* __restrict__ Fg, const double* __restrict__ Vg,
                              double sigma0, double t_est, double* t, MixResult* res, bool plus,
                              double delta0, int attempts, int iters) {
@@ -378,7 +378,7 @@ __device__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
 // iteration on M_sigma1 from u0 (in sm.u), FP64 Lanczos fallback.  On return
 // sm.u holds the unit null vector and *t the root.  plus: t+ end (else t-).
 // cold: no usable estimate (factor at sigma0 and go straight to Lanczos).
-__device__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+__device__ __noinline__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
                                const double* __restrict__ Fg, const double* __restrict__ Vg,
                                double* __restrict__ Q64, double sigma0, double t_est, bool cold,
                                double* t, MixResult* res, bool plus = true) {
@@ -511,7 +511,7 @@ __device__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw, MixSmem& sm
 
 // Stage 2 for one end: the double-float refinement, the FP64 one when it
 // does not converge (or without an estimate: cold).  u0 in sm.u.
-__device__ int refine_end(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+__device__ __noinline__ int refine_end(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
                           const double* __restrict__ Fg, const double* __restrict__ Vg,
                           double* __restrict__ Q64, double sigma0, double t_est, bool cold,
                           double* t, MixResult* res, bool plus) {
@@ -528,7 +528,7 @@ __device__ int refine_end(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
 //   Fg, Vg: packed FP64 F(p) and V (global).  sigma0: stage-1 shift.
 //   pred (learned warm start): the network's (log(t+/t_scale), u) for this
 //   line; the shift sigma1 = (1 - margin) t^ replaces stage 1.
-__device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
+__device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem& sm,
                                    const double* __restrict__ Fg, const double* __restrict__ Vg,
                                    float* __restrict__ Q32, double* __restrict__ Q64,
                                    double sigma0, bool want_min, bool stage2,
@@ -687,7 +687,7 @@ __device__ MixResult segment_mixed(const DevSpec& sp, const MixWork& mw, MixSmem
 // high parts are summed with TwoSum, the rounding errors of both kept in a
 // separate accumulator (Ogita, Rump, Oishi: Sum2 / Dot2).  Error ~ n eps^2 of
 // sum |terms| (eps = 2^-24).  Warp w takes the matrices j = w, w + 8, ...
-__device__ void contract_forms(const DevSpec& sp, const float2* __restrict__ Ahl, MixSmem& sm) {
+__device__ __noinline__ void contract_forms(const DevSpec& sp, const float2* __restrict__ Ahl, MixSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m;
   const long long P = sp.P;
@@ -760,7 +760,7 @@ __device__ void draw_direction(uint64_t seed, uint32_t chain, uint32_t step, dou
 // (Alg. 4), a rejected step (back to its start, F re-formed), the carried F,
 // the end of a step (next direction and length) and the queue of the next
 // wave.  sm.p, sm.v: the chain's point and direction.
-__device__ void complete_segment(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
+__device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
                                  MixSmem& sm, int r, int c, int status, double t_plus,
                                  double t_minus, double ell, int nrefl, double* __restrict__ Fc,
                                  const double* __restrict__ Vr, long long* st) {

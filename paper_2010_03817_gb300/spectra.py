@@ -49,6 +49,7 @@ def _bind(L):
     f("sp_spec_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
     f("sp_set_solver", [_vp, _i, _d, _d])
     f("sp_membership", [_vp, _i, _vp, _vp, _vp])
+    f("sp_set_mixed_solver", [_vp, _d, _d, _d, _i])
     f("sp_volume_estimate", [_vp, _d, _d, _d, _i, _i, _i, _i, _i, ctypes.c_uint64, _vp, _vp,
                              _vp])
     f("sp_intersect", [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp])
@@ -187,6 +188,11 @@ class Spectrahedron:
 
     def set_solver(self, kmax: int = 96, tol: float = 1e-13, sigma_frac: float = 0.1):
         _check(lib().sp_set_solver(self._h, kmax, tol, sigma_frac))
+
+    def set_mixed_solver(self, tol32: float = 1e-5, tol64: float = 1e-12, delta1: float = 2e-4,
+                         power_iters: int = 8):
+        """Stage-1 / stage-2 parameters of the mixed path (sp_set_mixed_solver)."""
+        _check(lib().sp_set_mixed_solver(self._h, tol32, tol64, delta1, power_iters))
 
     # -- primitives ---------------------------------------------------------
     def form_pencil(self, x=None, v=None, mode: str = "fp64", stream=None):
