@@ -412,6 +412,9 @@ def main():
         record = (torch.zeros((args.train_tuples, 2 * N_DIM), dtype=torch.float32, device="cuda"),
                   torch.zeros((args.train_tuples, 1 + M_DIM), dtype=torch.float32, device="cuda"),
                   torch.zeros(1, dtype=torch.int32, device="cuda"))
+    if learned:
+        # the recorded tuples carry the scales the network will be used with
+        spec.attach_mlp(None, x_scale=1.0 / TAU, t_scale=T_SCALE)
     t0 = time.perf_counter()
     state = burn_in(spectra, torch, spec, C, rank, args.burn_in, tau, record)
     burn_s = time.perf_counter() - t0

@@ -5,9 +5,11 @@
 #include <stdint.h>
 
 #ifndef SPG_THREADS
-#define SPG_THREADS 256
+#define SPG_THREADS 512
 #endif
 #define SPG_WARPS (SPG_THREADS / 32)
+// scratch of the blocked triangular solves: (SPG_WARPS + 1) x 32 partial sums
+#define SPG_SCR ((SPG_WARPS + 2) * 32)
 
 namespace spg {
 

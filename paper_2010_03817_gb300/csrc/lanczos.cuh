@@ -305,7 +305,7 @@ struct PencilOp {
   T* part;
 };
 
-// r <- M_sigma q.  z: scratch vector (m), s: scratch (>= 288)
+// r <- M_sigma q.  z: scratch vector (m), s: scratch (>= SPG_SCR)
 template <typename T>
 __device__ void apply_pencil(const PencilOp<T>& op, const T* q, T* r, T* z, int m, T* s) {
   for (int i = threadIdx.x; i < m; i += SPG_THREADS) z[i] = q[i];
@@ -327,7 +327,7 @@ struct LanczosOut {
 // Lanczos with full reorthogonalisation.
 //   q0 (m, smem): start vector (overwritten); Q (kmax x m, global): basis;
 //   ymax / ymin (m, smem): Ritz vectors of the extreme eigenvalues (ymin only
-//   if want_min); r, z (m, smem) and s (>= 288, smem): scratch.
+//   if want_min); r, z (m, smem) and s (>= SPG_SCR, smem): scratch.
 //   tol: relative residual target |M y - theta y| <= tol |theta|.
 template <typename T>
 __device__ LanczosOut lanczos_extreme(const PencilOp<T>& op, T* __restrict__ Q, T* q, T* r, T* z,

@@ -35,7 +35,7 @@ struct Smem {
   double* ymin;  // m
   double* u;     // m
   double* col;   // cholesky_scratch(m) (Cholesky panel)
-  double* scr;   // 288 + 32
+  double* scr;   // SPG_SCR (triangular-solve partial sums)
   LanczosScalars* sc;
   double* bc;    // small broadcast area (16 doubles)
   int* ib;       // small int broadcast area (16 ints)
@@ -66,7 +66,7 @@ __device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
   s.ymin = q; q += m;
   s.u = q; q += m;
   s.col = q; q += cholesky_scratch(m);
-  s.scr = q; q += 320;
+  s.scr = q; q += SPG_SCR;
   s.bc = q; q += 16;
   s.sc = reinterpret_cast<LanczosScalars*>(q);
   if (threadIdx.x == 0) s.sc->prof = nullptr;
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem) {
   const size_t P = (size_t)m * (m + 1) / 2;
   size_t d = (l_in_smem ? P : 0) + 4 * (size_t)n + (n + 1) + 6 * (size_t)m +
-             cholesky_scratch(m) + 320 + 16;
+             cholesky_scratch(m) + SPG_SCR + 16;
   size_t b = d * 8 + align8(sizeof(LanczosScalars)) + 16 * sizeof(int);
   return b;
 }

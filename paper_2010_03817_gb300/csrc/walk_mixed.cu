@@ -37,7 +37,7 @@ struct MixSmem {
   double* u;      // m
   double* um;     // m (null vector at t-)
   double* part;   // SPG_WARPS * m + 64
-  double* scr;    // 320
+  double* scr;    // SPG_SCR
   double* bc;     // 16
   float* q32;     // m
   float* r32;     // m
@@ -78,7 +78,7 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.u = d; d += m;
   s.um = d; d += m;
   s.part = d; d += (size_t)SPG_WARPS * m + 64;  // also the Cholesky panel
-  s.scr = d; d += 320;
+  s.scr = d; d += SPG_SCR;
   s.bc = d; d += 16;
   float* f = reinterpret_cast<float*>(d);
   s.q32 = f; f += m;
@@ -1168,7 +1168,7 @@ size_t mixed_region_bytes(int n, int m) {
 
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem) {
   size_t b = region_in_smem ? ((mixed_region_bytes(n, m) + 15) & ~size_t(15)) : 0;
-  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 64 + 320 + 16);
+  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 64 + SPG_SCR + 16);
   b += 4 * (size_t)14 * m;
   b += sizeof(LanczosScalars) + 16 * sizeof(int);
   return b;
