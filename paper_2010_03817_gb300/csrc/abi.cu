@@ -768,6 +768,9 @@ static int ensure_chain_mixed(sp_chains* ch) {
 // Mixed path: waves of one segment per active chain.  Each wave forms V for
 // the active chains on the tensor cores, then runs the mixed segment kernel,
 // which queues the chains that still have steps to do for the next wave.
+// waves with at most this many chains contract the normals in-kernel
+constexpr int kDeferMinRows = 256;
+
 static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rho, double kappa,
                           bool learned, void* stream) {
   sp_spec* s = ch->spec;
@@ -871,11 +874,15 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
       ch->n_mlp += 5;  // features, conversion, 3 GEMMs
     }
     if (ch->timing) cudaEventRecord(ev[2], st);
+    // small waves (the tail of chains with many reflections) contract
+    // in-kernel: the tensor-core GEMM's cost hardly shrinks with the rows
+    const bool defer_now = defer && count > kDeferMinRows;
+    wv.pend = defer_now ? ch->ms.pend : nullptr;
     if (e == cudaSuccess) e = launch_mixed_wave(ds, mw, wv, st);
     if (ch->timing) cudaEventRecord(ev[3], st);
     ch->n_wave += 1;
     if (e != cudaSuccess) return cuda_fail(e, "walk wave launch");
-    if (defer) {
+    if (defer_now) {
       e = launch_ozaki_contract(ch->ms.Ubuf, count, s->n, s->m, s->Bc, s->ecolc, ch->ms.udig,
                                 ch->ms.uerow, ch->ms.Wpart, ch->ms.err, st);
       if (ch->timing) cudaEventRecord(ev[4], st);
@@ -888,12 +895,12 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
     cur ^= 1;
     if (ch->timing) {
       // the next wave's count copy synchronises the stream; read this wave's events
-      cudaEventSynchronize(defer ? ev[5] : ev[3]);
+      cudaEventSynchronize(defer_now ? ev[5] : ev[3]);
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
       cudaEventElapsedTime(&a0, ev[0], ev[1]);
       cudaEventElapsedTime(&a1, ev[1], ev[2]);
       cudaEventElapsedTime(&a2, ev[2], ev[3]);
-      if (defer) {
+      if (defer_now) {
         cudaEventElapsedTime(&a3, ev[3], ev[4]);
         cudaEventElapsedTime(&a4, ev[4], ev[5]);
       }
