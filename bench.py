@@ -533,7 +533,7 @@ def main():
                 "ms_per_step": r["dev_ms"] / r["steps"],
                 "segments_per_step": s["segments"] / (C * r["steps"]),
                 "iters_per_segment": s["lanczos_iters"] / segs,
-                "fp64_power_iters_per_segment": s["power_iters"] / segs,
+                "power_iters_per_segment": s["power_iters"] / segs,
                 "fp64_fallback_rate": s["fp64_fallbacks"] / segs,
                 "warm_start_accept_rate": s["learned_ok"] / segs,
                 "bad_steps": s["bad_steps"], "steps": r["steps"]}

@@ -53,9 +53,10 @@ extern "C" {
 
 /* arithmetic modes */
 #define SP_MODE_FP64 0   /* every step in FP64 */
-#define SP_MODE_MIXED 1  /* tensor-core V formation (exact digit splitting, FP64 quality),
-                            FP32 estimate, FP64 factorisation next to the boundary and FP64
-                            refinement of t+ and u; needs n <= 224 */
+#define SP_MODE_MIXED 1  /* tensor-core V formation and normals (exact digit splitting,
+                            FP64 quality), FP32 estimate, double-float factorisation next to
+                            the boundary and refinement of t+ and u (FP64 as the fallback);
+                            needs n <= 224 (normals on the tensor cores: m <= 224) */
 #define SP_MODE_LEARNED 2  /* the mixed path with the network's warm start (sp_attach_mlp)
                               for the Billiard walk; primitives run as SP_MODE_MIXED */
 
@@ -66,8 +67,8 @@ extern "C" {
 #define SP_STAT_LANCZOS 3      /* Lanczos iterations */
 #define SP_STAT_SHIFT_RETRY 4  /* shifted factorisations redone unshifted */
 #define SP_STAT_NOCONV 5       /* eigen-solves that hit the iteration cap */
-#define SP_STAT_FALLBACK 6     /* mixed path: segments that fell back to an FP64 Lanczos */
-#define SP_STAT_POWER 7        /* mixed path: FP64 power iterations next to the boundary */
+#define SP_STAT_FALLBACK 6     /* mixed path: segments whose stage 2 fell back to FP64 */
+#define SP_STAT_POWER 7        /* mixed path: power iterations next to the boundary */
 #define SP_STAT_LEARNED_OK 8   /* learned path: warm starts accepted by the certificate */
 #define SP_STAT_LEARNED_MISS 9 /* learned path: warm starts rejected (plain stage 1 instead) */
 #define SP_NUM_STATS 12

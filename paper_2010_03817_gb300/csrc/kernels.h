@@ -33,7 +33,7 @@ enum StatSlot : int {
   kStatShiftRetry = 4,   // shifted factorisations that failed and were redone unshifted
   kStatNoConv = 5,       // eigen-solves that hit the iteration cap
   kStatFallback = 6,     // mixed path: FP64 Lanczos fallbacks
-  kStatPower = 7,        // mixed path: FP64 power iterations
+  kStatPower = 7,        // mixed path: power iterations next to the boundary
   kStatLearnedOk = 8,    // learned path: warm starts accepted by the certificate
   kStatLearnedMiss = 9,  // learned path: warm starts rejected (plain stage 1 instead)
   kNumStats = 12,

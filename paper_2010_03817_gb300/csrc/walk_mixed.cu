@@ -3,17 +3,19 @@
 //   F(p) is carried in FP64 from segment to segment (F <- F + t V).
 //   Stage 1 (FP32): Cholesky of F + sigma0 V and Lanczos on
 //     M = -L^{-1} V L^{-T} give an estimate t~ of t+ (Alg. 2) and u0.
-//   Stage 2 (FP64): Cholesky of F + sigma1 V with sigma1 just below t~ --
-//     the near-singular factorisation at the boundary stays in FP64 -- then a
-//     few power iterations on M_sigma1, whose dominant eigenvalue
-//     1/(t+ - sigma1) is separated by orders of magnitude, give t+ and the
-//     null vector u to FP64 accuracy.  Success of that factorisation
-//     certifies that F + sV > 0 on [0, sigma1], so the root found is the
-//     smallest positive one (Lemma "PEP and S cap C").
-//   Stage 3: normal w_j = u^T A_j u (Lemma "Gradient of det F") by a
-//     double-float (FP32 pair) contraction; reflection (Eq. "reflection").
-// t- (Hit-and-Run / intersection) comes from stage 1 refined by the FP64
-// pencil Rayleigh quotient -(u^T F u)/(u^T V u) with the exact F and V.
+//   Stage 2 (double-float, FP64 as the fallback): Cholesky of F + sigma1 V
+//     with sigma1 just below t~ -- the near-singular factorisation next to
+//     the boundary needs more than FP32 -- then a few power iterations on
+//     M_sigma1, whose dominant eigenvalue 1/(t+ - sigma1) is separated by
+//     orders of magnitude, give t+ and the null vector u.  Success of that
+//     factorisation certifies that F + sV > 0 on [0, sigma1], so the root
+//     found is the smallest positive one (Lemma "PEP and S cap C").
+//   Stage 3: normal w_j = u^T A_j u (Lemma "Gradient of det F") on the
+//     tensor cores for a whole wave (ozaki.cu), or in-kernel by a
+//     double-float contraction; reflection (Eq. "reflection").
+// t- (Hit-and-Run / intersection) comes from stage 1 refined by the pencil
+// Rayleigh quotient -(u^T F u)/(u^T V u) with the exact F and V
+// (double-float) and stage 2 on the negative side.
 #include <math.h>
 
 #include "common.cuh"
@@ -471,7 +473,7 @@ __device__ __noinline__ int refine_end_fp64(const DevSpec& sp, const MixWork& mw
   } else {
     invert_diag_blocks<double>(G64, m);
   }
-  stage_mark(mw, 3, tmark);  // FP64 power iterations
+  stage_mark(mw, 3, tmark);  // FP64 power iterations (fallback)
   if (!converged) {
     res->fallback = 1;
     // robust fallback: FP64 Lanczos for the extreme eigenvalue of this end
