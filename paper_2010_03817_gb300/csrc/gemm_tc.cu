@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   for (int kt = 0; kt < KT; ++kt) {
     const int buf = kt & 1;
     const bool w = kt < 2 || tc::mbar_wait(&mbar[buf], ((kt - 2) >> 1) & 1);
-    if (!__syncthreads_and(w)) {  // a block-uniform verdict
+    if (!__syncthreads_and(w)) {  // a block-uniform decision
       ok = false;
       break;
     }

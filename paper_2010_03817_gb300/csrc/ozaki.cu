@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int s = 0; s < kDigits; ++s) {
     if (s + 1 < kDigits) {
       // buffer (s + 1) & 1 was last read by the MMAs of plane s - 1; the
-      // verdict of the bounded wait is made block-uniform
+      // outcome of the bounded wait is made block-uniform
       const bool w = s < 1 || tc::mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1);
       if (!__syncthreads_and(w)) {
         ok = false;
