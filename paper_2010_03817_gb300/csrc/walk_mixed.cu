@@ -46,15 +46,13 @@ struct MixSmem {
   float* z32;     // m
   float* y32;     // m
   float* ym32;    // m
-  float* col32;   // m
+  float* pad32;   // m: keeps the number of m-float arrays even (alignment)
   float* duh;     // m: u as an FP32 pair (stage 2)
   float* dul;     // m
   float* dfh;     // m: F u (pair)
   float* dfl;     // m
   float* dgh;     // m: V u (pair)
   float* dgl;     // m
-  float* d32;     // m: residual / correction
-  float* x32;     // m
   LanczosScalars* sc;
   int* ib;        // 16
 };
@@ -88,15 +86,14 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.z32 = f; f += m;
   s.y32 = f; f += m;
   s.ym32 = f; f += m;
-  s.col32 = f; f += m;
+  s.pad32 = f; f += m;
   s.duh = f; f += m;
   s.dul = f; f += m;
   s.dfh = f; f += m;
   s.dfl = f; f += m;
   s.dgh = f; f += m;
   s.dgl = f; f += m;
-  s.d32 = f; f += m;
-  s.x32 = f; f += m;  // 14 m floats: the next address stays 8-byte aligned
+  // 12 m floats: the next address stays 8-byte aligned
   s.sc = reinterpret_cast<LanczosScalars*>(f);
   if (threadIdx.x == 0) s.sc->prof = nullptr;
   s.ib = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(s.sc) + sizeof(LanczosScalars));
@@ -1171,7 +1168,7 @@ size_t mixed_region_bytes(int n, int m) {
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem) {
   size_t b = region_in_smem ? ((mixed_region_bytes(n, m) + 15) & ~size_t(15)) : 0;
   b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 64 + SPG_SCR + 16);
-  b += 4 * (size_t)14 * m;
+  b += 4 * (size_t)12 * m;
   b += sizeof(LanczosScalars) + 16 * sizeof(int);
   return b;
 }
