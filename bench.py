@@ -323,6 +323,11 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
         if float(lz.sum()) > 0:
             share["lanczos_split"] = {nm: float(lz[i] / lz.sum()) for i, nm in
                                       enumerate(["apply", "reorth", "check", "final"])}
+        s2 = tot[12:16]
+        if float(s2.sum()) > 0:
+            share["stage2_iteration_split"] = {
+                nm: float(s2[i] / s2.sum()) for i, nm in
+                enumerate(["solve_upper", "symv_V", "solve_lower", "reductions"])}
     return dict(chains=chains, dev_ms=dev_ms, wall=wall, stats=stats, kt=kt, share=share,
                 steps=steps)
 

@@ -323,7 +323,9 @@ int sp_kernel_timing(sp_chains* ch, int enable, double* out);
  * float, or FP64 on the fallback), 3 stage-2 power iterations, 4 FP64
  * Lanczos fallback, 5 normal contraction, 6 bookkeeping; and inside every
  * Lanczos run: 8 operator application, 9 reorthogonalisation, 10
- * convergence checks, 11 final Ritz pairs.
+ * convergence checks, 11 final Ritz pairs; and inside the double-float
+ * power iterations: 12 L^{-T} solve, 13 product with V, 14 L^{-1} solve,
+ * 15 reductions and vector updates.
  */
 int sp_set_stage_timers(sp_spec* s, long long* timers);
 

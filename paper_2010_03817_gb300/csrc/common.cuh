@@ -76,6 +76,15 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// CTA-wide: ask the L2 to fetch [p, p + bytes) (one prefetch per 128-byte
+// line), so that later passes over the range find it there instead of
+// paying the DRAM latency row by row
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 // broadcast from lane src (overloaded for the double-float type)
 __device__ __forceinline__ float shfl_idx(float v, int src) {
   return __shfl_sync(0xffffffffu, v, src);

@@ -104,7 +104,7 @@ struct MixWork {
   int ctas;
   long long* prof;  // optional: per-CTA clock64 sums per stage (kProfSlots each)
 };
-constexpr int kProfSlots = 16;  // 0-6: stages, 8-11: Lanczos sub-stages
+constexpr int kProfSlots = 16;  // 0-6: stages, 8-11: Lanczos, 12-15: stage-2 iteration parts
 
 struct MixWave {
   int kind, C, steps, rho;

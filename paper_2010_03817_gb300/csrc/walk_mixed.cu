@@ -332,10 +332,14 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
       z[i] = y[i];
     }
     __syncthreads();
+    long long ts = clock64();
     // r = M y = -L^{-1} V L^{-T} y
     solve_upper<T>(G, z, m, scr);
+    stage_mark(mw, 12, ts);
     symv_packed<T, double>(Vg, z, r, m, T(-1), part);
+    stage_mark(mw, 13, ts);
     solve_lower<T>(G, r, m, scr);
+    stage_mark(mw, 14, ts);
     T b(0);
     for (int i = tid; i < m; i += SPG_THREADS) b += y[i] * r[i];
     const T mut = block_sum(b, red);
@@ -348,6 +352,7 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
     mu = to_double(mut);
     for (int i = tid; i < m; i += SPG_THREADS) y[i] = r[i];
     __syncthreads();
+    stage_mark(mw, 15, ts);  // reductions and vector updates
     ++res->power;
     if (res2 <= mw.tol64 * mw.tol64 * mu * mu) {
       converged = true;
@@ -546,6 +551,10 @@ __device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork
   float* G32 = reinterpret_cast<float*>(sm.R);
   float* V32 = G32 + P;
   long long tmark = clock64();
+  // F and V are read by both fills and by every product with V of stage 2:
+  // bring them into the L2 once, all lines at a time
+  prefetch_l2(Fg, sizeof(double) * (size_t)P);
+  prefetch_l2(Vg, sizeof(double) * (size_t)P);
 
   // ---------------- stage 1 with the learned warm start ---------------------
   // The network predicts t+ and the null vector u.  Stage 1 factors at
