@@ -71,7 +71,7 @@ def parse():
     p.add_argument("--tol32", type=float, default=None,
                    help="stage-1 FP32 Lanczos tolerance of the mixed paths (library default 1e-5)")
     p.add_argument("--tol64", type=float, default=None,
-                   help="stage-2 relative residual of the mixed paths (library default 1e-11)")
+                   help="stage-2 relative residual of the mixed paths (library default 1e-12)")
     p.add_argument("--train-tuples", type=int, default=262144)
     p.add_argument("--train-epochs", type=int, default=24)
     return p.parse_args()
@@ -407,7 +407,7 @@ def main():
     A = workload()
     spec = spectra.Spectrahedron(A)
     if args.tol32 is not None or args.tol64 is not None:
-        spec.set_mixed_solver(tol32=args.tol32 or 1e-4, tol64=args.tol64 or 1e-11)
+        spec.set_mixed_solver(tol32=args.tol32 or 1e-4, tol64=args.tol64 or 1e-12)
     tau = TAU * args.tau_scale
     C = args.chains
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

@@ -125,6 +125,7 @@ struct MixSpace {
   double* Frows = nullptr;    // rows x P
   double* Vrows = nullptr;    // rows x P
   int* err = nullptr;
+  float2* vdf = nullptr;      // ctas x P: V as double-float pairs for stage 2
   // deferred normals of a wave (tensor-core contraction)
   double* Ubuf = nullptr;     // rows x m
   double* Tbuf = nullptr;     // rows
@@ -135,7 +136,8 @@ struct MixSpace {
   int wtiles = 0;
   void release() {
     cudaFree(Q32); cudaFree(Q64); cudaFree(region); cudaFree(digits); cudaFree(erow);
-    cudaFree(Frows); cudaFree(Vrows); cudaFree(err);
+    cudaFree(Frows); cudaFree(Vrows); cudaFree(err); cudaFree(vdf);
+    vdf = nullptr;
     cudaFree(Ubuf); cudaFree(Tbuf); cudaFree(pend); cudaFree(Wpart); cudaFree(udig);
     cudaFree(uerow);
     Q32 = nullptr; Q64 = nullptr; region = nullptr; digits = nullptr; erow = nullptr;
@@ -179,6 +181,7 @@ struct MixSpace {
               cudaMalloc(&erow, sizeof(int) * rows) == cudaSuccess &&
               cudaMalloc(&Vrows, sizeof(double) * P * rows) == cudaSuccess &&
               (!with_f || cudaMalloc(&Frows, sizeof(double) * P * rows) == cudaSuccess) &&
+              cudaMalloc(&vdf, sizeof(float2) * P * ctas) == cudaSuccess &&
               cudaMalloc(&err, sizeof(int)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -207,7 +210,7 @@ struct sp_spec {
   uint16_t* Bc = nullptr;  // digits of the rows (j, i) of A_j: tensor-core normals
   int* ecolc = nullptr;
   int kmax32 = 96, kmax64 = 96, power_iters = 8;
-  double tol32 = 1e-4, tol64 = 1e-11, delta1 = 2e-4;
+  double tol32 = 1e-4, tol64 = 1e-12, delta1 = 2e-4;
   long long* prof = nullptr;  // optional stage timers (device, ctas x kProfSlots)
   int learned_iters = 12;
   // learned warm start
@@ -221,6 +224,7 @@ struct sp_spec {
     w.Q64 = sp_.Q64;
     w.region_global = sp_.region;
     w.region_bytes = sp_.region_bytes;
+    w.vdf = sp_.vdf;
     w.kmax32 = kmax32;
     w.kmax64 = kmax64;
     w.power_iters = power_iters;

@@ -98,6 +98,7 @@ struct MixWork {
   float* Q32;               // per CTA: kmax32 * m (FP32 Lanczos basis)
   double* Q64;              // per CTA: kmax64 * m (FP64 fallback basis)
   uint8_t* region_global;   // per CTA work region when it does not fit in shared memory
+  float2* vdf;              // per CTA: P double-float entries of stage 2's V
   size_t region_bytes;
   int kmax32, kmax64, power_iters, learned_iters;
   double tol32, tol64, delta1, sigma_frac;

@@ -290,6 +290,8 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
   T* part = reinterpret_cast<T*>(sm.part);
   T* scr = reinterpret_cast<T*>(sm.scr);
   T* red = reinterpret_cast<T*>(sm.sc->red);
+  // V as pairs, split once for all power iterations (global, per block)
+  T* Vd = reinterpret_cast<T*>(mw.vdf) + (size_t)blockIdx.x * P;
   long long tmark = clock64();
   double sigma1 = sigma0;
   bool ok = false;
@@ -297,7 +299,11 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
   for (int attempt = 0; attempt < attempts && !ok; ++attempt) {
     sigma1 = sigma0 + (t_est - sigma0) * (1.0 - delta);
     const T s1(sigma1);
-    for (long long e = tid; e < P; e += SPG_THREADS) G[e] = T(Fg[e]) + s1 * T(Vg[e]);
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const T ve(Vg[e]);
+      Vd[e] = ve;
+      G[e] = T(Fg[e]) + s1 * ve;
+    }
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
     ok = factor_cholesky<T>(G, m, part, &sm.ib[0]);
@@ -336,7 +342,7 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
     // r = M y = -L^{-1} V L^{-T} y
     solve_upper<T>(G, z, m, scr);
     stage_mark(mw, 12, ts);
-    symv_packed<T, double>(Vg, z, r, m, T(-1), part);
+    symv_packed<T>(Vd, z, r, m, T(-1), part);
     stage_mark(mw, 13, ts);
     solve_lower<T>(G, r, m, scr);
     stage_mark(mw, 14, ts);
