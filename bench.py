@@ -184,23 +184,25 @@ def run_reference(args):
     oracle.build()
     A = workload()
     times, segs = [], 0
+    chains = 32  # as the cpu_baseline of the GPU arm: two chains per host core of the box
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(A, TAU, chains=16, steps=1)
+        r = cpu_oracle_rate(A, TAU, chains=chains, steps=1)
         if i >= args.warmup:
             times.append(r["seconds"])
             segs += r["segments"]
     total = sum(times)
-    value = 16 * args.steps / total
+    value = chains * args.steps / total
     line = {
         "impl": "reference", "metric": "billiard steps/s at n=m=200", "value": value,
         "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (oracle sample: 16 chains x 1 step per bench step)"},
+        "config": {"workload": WORKLOAD + " (oracle sample: %d chains x 1 step per bench step)"
+                               % chains},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": "16 chains x 1 Billiard step per bench step, %d segments"
-                                   % segs},
+                         "sample": "%d chains x 1 Billiard step per bench step, %d segments"
+                                   % (chains, segs)},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
