@@ -72,6 +72,8 @@ def parse():
                    help="stage-1 FP32 Lanczos tolerance of the mixed paths (library default 1e-5)")
     p.add_argument("--tol64", type=float, default=None,
                    help="stage-2 relative residual of the mixed paths (library default 1e-12)")
+    p.add_argument("--check-samples", type=int, default=384,
+                   help="boundary-oracle calls of each timed walk checked against the oracle")
     p.add_argument("--train-tuples", type=int, default=262144)
     p.add_argument("--train-epochs", type=int, default=24)
     return p.parse_args()
@@ -161,35 +163,48 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU baseline: the oracle on the host cores
 # ----------------------------------------------------------------------------
-def cpu_oracle_rate(A, tau, chains=32, steps=1):
+def cpu_oracle_rate(A, tau, X, step0, chains=32, steps=1):
+    """The oracle's Billiard walk on chains 0..chains-1 from the points X
+    (chains x n, host) over steps step0 .. step0+steps-1: the same chains,
+    states and Philox draws as the GPU arms' first timed steps."""
     import oracle
-    X0 = start_points(chains, 0)
     t0 = time.perf_counter()
-    _, stats = oracle.walk("billiard", A, X0, steps, tau=tau, rho=RHO, kappa=KAPPA,
-                           seed=SEED_WALK)
+    _, stats = oracle.walk("billiard", A, np.ascontiguousarray(X[:chains]), steps, tau=tau,
+                           rho=RHO, kappa=KAPPA, seed=SEED_WALK, step0=step0, chain0=0)
     dt = time.perf_counter() - t0
     return dict(value=chains * steps / dt, unit="steps/s", cores=oracle.num_threads(),
-                kind="oracle",
-                sample="%d chains x %d Billiard step(s) of the same workload (%d segments), "
-                       "%.1f s on %d threads" % (chains, steps, stats["segments"], dt,
-                                                 oracle.num_threads()),
+                kind="oracle", segments_per_s=stats["segments"] / dt,
+                sample="chains 0-%d of the burned-in state, steps %d-%d (the GPU arms' first "
+                       "timed steps), %d segments, %.1f s on %d threads"
+                       % (chains - 1, step0, step0 + steps - 1, stats["segments"], dt,
+                          oracle.num_threads()),
                 segments=stats["segments"], seconds=dt)
 
 
 def run_reference(args):
+    """The oracle (FP64, Cholesky + Jacobi, OpenMP over chains) on the GPU
+    arms' workload and step window: chains 0..31 from the same start cloud
+    walk the same burn-in and warm-up steps (untimed), then the --steps timed
+    steps, each a bounded sample of the bench step (32 of the 8192 chains)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
     A = workload()
+    chains = 32  # two chains per host core of the box
+    X = start_points(CHAINS, 0)[:chains]
+    X, _ = oracle.walk("billiard", A, X, args.burn_in + args.warmup, tau=TAU, rho=RHO,
+                       kappa=KAPPA, seed=SEED_WALK, step0=0, chain0=0)
     times, segs = [], 0
-    chains = 32  # as the cpu_baseline of the GPU arm: two chains per host core of the box
-    for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(A, TAU, chains=chains, steps=1)
-        if i >= args.warmup:
-            times.append(r["seconds"])
-            segs += r["segments"]
+    step = args.burn_in + args.warmup
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        X, st = oracle.walk("billiard", A, X, 1, tau=TAU, rho=RHO, kappa=KAPPA, seed=SEED_WALK,
+                            step0=step, chain0=0)
+        times.append(time.perf_counter() - t0)
+        segs += st["segments"]
+        step += 1
     total = sum(times)
     value = chains * args.steps / total
     line = {
@@ -197,12 +212,17 @@ def run_reference(args):
         "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (oracle sample: %d chains x 1 step per bench step)"
-                               % chains},
+        "config": {"workload": WORKLOAD + " (oracle sample: chains 0-%d, the GPU arms' timed "
+                               "steps %d-%d)" % (chains - 1, args.burn_in + args.warmup,
+                                                 step - 1)},
+        "oracle_calls_per_s": segs / total,
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": "%d chains x 1 Billiard step per bench step, %d segments"
-                                   % (chains, segs)},
+                         "sample": "chains 0-%d x %d burned-in Billiard steps (%d segments, "
+                                   "%.1f segments per chain-step), %.1f s"
+                                   % (chains - 1, args.steps, segs, segs / (chains * args.steps),
+                                      total),
+                         "segments_per_s": segs / total},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -224,14 +244,23 @@ def alg_flops_fp64(n, m, stats, steps):
 
 
 def alg_flops_wave(n, m, stats):
-    """Algorithmic flops of the mixed wave kernel: per segment two Cholesky
-    factorisations (m^3/3 each: FP32 at the stage-1 shift, double-float next to
-    the boundary), their fills (2P each) and the carried-F update (2P); 4m^2
-    per Lanczos or power iteration (two triangular solves and a product with
-    V)."""
-    P = m * (m + 1) / 2
-    return (stats["segments"] * (2 * m ** 3 / 3 + 6 * P)
+    """The method's own work in the mixed wave kernel (the factorisation and
+    the eigen-solve of INTERSECTION): one Cholesky (m^3/3) per segment and
+    4m^2 per iteration of the eigen-solve (two triangular solves and a product
+    with V), counting the FP32 Lanczos and the double-float power iterations.
+    The mixed path's second factorisation (double-float, next to the
+    boundary) and its fills are overhead of the precision scheme, reported
+    apart (alg_overhead_wave)."""
+    return (stats["segments"] * m ** 3 / 3
             + (stats["lanczos_iters"] + stats["power_iters"]) * 4 * m * m)
+
+
+def alg_overhead_wave(n, m, stats):
+    """Flops the mixed wave kernel spends beyond the method's work: the
+    second (double-float) factorisation per segment and the fills of both
+    (2P each) and the carried-F update (2P)."""
+    P = m * (m + 1) / 2
+    return stats["segments"] * (m ** 3 / 3 + 6 * P)
 
 
 def alg_flops_contraction(n, m, segments):
@@ -250,13 +279,41 @@ def alg_flops_formation(n, m, segments):
     return segments * 28 * 2 * Kp * P
 
 
+def alg_flops_fp64_formation(n, m, segments):
+    """FP64-quality flops of V = sum v_j A_j (2nP per segment): what the
+    digit-split tensor-core formation delivers."""
+    return segments * 2 * n * m * (m + 1) / 2
+
+
+def alg_flops_fp64_contraction(n, m, segments):
+    """FP64-quality flops of w_j = u^T A_j u (2(n+1)P per normal)."""
+    return segments * 2 * (n + 1) * m * (m + 1) / 2
+
+
+# ALU peaks from the unit counts and the 2.07 GHz maximum SM clock of GB300
+# (152 SMs): FP32 128 FFMA / clk / SM, FP64 2 DFMA / clk / SM; a dependent-FMA
+# probe on this GPU measured 69.8 (FP32) and 1.19 (FP64) TFLOP/s.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+PROBE_FP32_TFLOPS, PROBE_FP64_TFLOPS = 69.8, 1.19
+# dram__bytes_read.sum + dram__bytes_write.sum of mixed_wave_kernel per
+# segment (ncu, one wave of 152 lines of this workload; the carried F and V
+# read, F written); None once the kernel changes until the next capture
+WAVE_DRAM_BYTES_PER_SEGMENT = None
+FP64_DRAM_BYTES_PER_SEGMENT = None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         d = json.load(open(path))
-        return {"bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+        return {"bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained",
+                                                     d["bf16_tflops"])),
+                "hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "source": "measured"}
     except (OSError, ValueError, KeyError):
-        return {"bf16_tflops": 1900.0, "source": "fallback"}
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+                "source": "fallback"}
 
 
 # ----------------------------------------------------------------------------
@@ -278,7 +335,10 @@ def burn_in(spectra, torch, spec, C, rank, steps, tau, record=None):
 
 
 def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, state,
-              stage_timers=False):
+              stage_timers=False, record=0):
+    """Warm-up steps, then the timed steps as one walk call.  record > 0:
+    about that many of the timed walk's boundary-oracle calls are recorded
+    (sp_record_segments, evenly sampled by arrival) for the oracle check."""
     chains = spectra.Chains(spec, C, x0=start_points(C, rank), seed=SEED_WALK,
                             chain0=replica_plan(rank, 1, C)["chain0"])
     chains.set_state(state[0], state[1])
@@ -287,6 +347,16 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
         chains.billiard(1, tau=tau, rho=RHO, kappa=KAPPA, mode=mode)
     torch.cuda.synchronize()
     _, s0 = chains.status()
+    warm_state = chains.state_host()
+    seg = None
+    if record > 0:
+        # sampling stride from the warm-up's segments per step
+        est = max(1, s0["segments"] * steps // max(1, warmup))
+        every = max(1, est // record)
+        buf = torch.zeros((2 * record, 3 * spec.n + 8), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        chains.record_segments(buf, cnt, every)
+        seg = (buf, cnt, every)
     timers = None
     if stage_timers and mode != "fp64":
         sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -306,6 +376,9 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
     ev1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    if seg is not None:
+        chains.record_segments()
+        seg = spectra.decode_segments(seg[0], int(seg[1].item()), seg[2], spec.n)
     evs = [(ev0, ev1)]
     kt = chains.kernel_timing(0)
     dev_ms = float(sum(a.elapsed_time(b) for a, b in evs))
@@ -331,27 +404,34 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
                 nm: float(s2[i] / s2.sum()) for i, nm in
                 enumerate(["solve_upper", "symv_V", "solve_lower", "reductions"])}
     return dict(chains=chains, dev_ms=dev_ms, wall=wall, stats=stats, kt=kt, share=share,
-                steps=steps)
+                steps=steps, warm_state=warm_state, segments=seg)
 
 
-def oracle_check(spectra, torch, spec, A, chains, mode, samples):
-    """t+ and normal of sampled walk states (x, v) against the FP64 oracle."""
+def oracle_check(A, seg, tol):
+    """t+ and the unit normal of the timed walk's own recorded boundary-oracle
+    calls (sp_record_segments, sampled over the whole timed window) against
+    the FP64 oracle on the same lines.  The normal is compared for segments
+    that reflected, where the eigengap allows (relative gap > 1e-6)."""
     import oracle
-    from paper_2010_03817_gb300 import workloads as W
-    x, _ = chains.state()
-    X = x[:samples].cpu().numpy()
-    V = W.random_directions(N_DIM, samples, seed=77)
-    tp, wh, s, st = spec.reflect(torch.tensor(X, device="cuda"), torch.tensor(V, device="cuda"),
-                                 mode=mode)
-    tp, wh, st = tp.cpu().numpy(), wh.cpu().numpy(), st.cpu().numpy()
-    et, ew = 0.0, 0.0
-    for c in range(samples):
-        r = oracle.reflect(A, X[c], V[c])
-        et = max(et, abs(tp[c] - r["t_plus"]) / abs(r["t_plus"]))
-        if r["rel_gap"] > 1e-6:
-            ew = max(ew, float(np.abs(wh[c] - r["w_hat"]).max()))
-    return {"t_rel_err_max": et, "normal_err_max": ew, "samples": samples,
-            "status_ok": bool((st == 0).all())}
+    ok = seg["status"] == 0
+    P, V = seg["p"][ok], seg["v"][ok]
+    ref = oracle.reflect_batch(A, P, V)
+    good = ref["status"] == 0
+    et = np.abs(seg["t_plus"][ok][good] - ref["t_plus"][good]) / np.abs(ref["t_plus"][good])
+    refl = seg["reflected"][ok][good] & (ref["rel_gap"][good] > 1e-6)
+    ew = np.abs(seg["w_hat"][ok][good][refl] - ref["w_hat"][good][refl]).max(axis=1) \
+        if refl.any() else np.zeros(0)
+    out = {"samples": int(good.sum()), "reflected_samples": int(refl.sum()),
+           "t_rel_err_max": float(et.max()) if len(et) else None,
+           "t_rel_err_p99": float(np.quantile(et, 0.99)) if len(et) else None,
+           "t_rel_err_median": float(np.median(et)) if len(et) else None,
+           "normal_err_max": float(ew.max()) if len(ew) else None,
+           "normal_err_p99": float(np.quantile(ew, 0.99)) if len(ew) else None,
+           "oracle_failures": int((~good).sum()), "gpu_non_ok": int((~ok).sum()),
+           "tolerance": tol}
+    out["pass"] = bool(len(et) >= 256 and et.max() <= tol and
+                       (len(ew) == 0 or ew.max() <= tol))
+    return out
 
 
 def train_network(spectra, torch, spec, X, Y, cnt, epochs, record_s, walk_steps):
@@ -440,12 +520,14 @@ def main():
             if mode == args.mode:
                 continue
             context[mode] = time_path(spectra, torch, spec, mode, C, rank, args.steps,
-                                      args.warmup, tau, flush, state)
+                                      args.warmup, tau, flush, state,
+                                      record=0 if args.no_check else args.check_samples)
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
         head = time_path(spectra, torch, spec, args.mode, C, rank, args.steps, args.warmup, tau,
-                         flush, state, stage_timers=args.stage_timers)
+                         flush, state, stage_timers=args.stage_timers,
+                         record=0 if args.no_check else args.check_samples)
     if world > 1:
         dist.barrier()
     times = [head["dev_ms"]]
@@ -457,41 +539,63 @@ def main():
     st = head["stats"]
     kt = head["kt"]
 
-    # roofline of the dominant kernel of the headline path (FP64 pipe)
+    # roofline of the dominant kernel of the headline path: the method's own
+    # work (one factorisation and the eigen-solve iterations per segment, plus
+    # formation and normal on the FP64 path) over its CUDA-event time, against
+    # the ALU peak from the unit counts and the maximum clock
+    P = M_DIM * (M_DIM + 1) / 2
     if args.mode == "fp64":
         flops = alg_flops_fp64(N_DIM, M_DIM, st, C * args.steps)
         ms = kt["fp64_ms"] or head["dev_ms"]
         roof = {"bound": "alu", "kernel": "walk_fp64_kernel",
                 "launches": int(kt["fp64_launches"])}
-        peak, unit = 152 * 2 * 2 * 2.07e9 / 1e12, "TFLOP/s (FP64)"  # 2 DFMA/clk/SM
+        peak, probe, unit = PEAK_FP64_TFLOPS, PROBE_FP64_TFLOPS, "TFLOP/s (FP64 pipe)"
+        dram = FP64_DRAM_BYTES_PER_SEGMENT
+        overhead = 0.0
     else:
         flops = alg_flops_wave(N_DIM, M_DIM, st)
         ms = kt["wave_ms"] or head["dev_ms"]
         roof = {"bound": "alu", "kernel": "mixed_wave_kernel",
                 "launches": int(kt["wave_launches"])}
-        peak, unit = 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s (FP32 pipe)"  # 128 FFMA/clk/SM
+        peak, probe, unit = PEAK_FP32_TFLOPS, PROBE_FP32_TFLOPS, "TFLOP/s (FP32 pipe)"
+        dram = WAVE_DRAM_BYTES_PER_SEGMENT
+        overhead = alg_overhead_wave(N_DIM, M_DIM, st)
     achieved = flops / (ms / 1e3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "unit": unit,
-                 "frac": achieved / peak, "traffic": None,
-                 "kernel_ms_per_step": ms / args.steps,
-                 "share_of_step": ms / max(1e-9, head["dev_ms"])})
+    launches = max(1, roof["launches"])
+    roof.update({
+        "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+        "peak_source": "derived: 152 SMs x unit count x 2.07 GHz", "peak_probe": probe,
+        "frac_of_probe": achieved / probe,
+        "traffic": (dram * st["segments"] / launches) if dram else None,
+        "traffic_unit": "bytes per launch (DRAM read + write)",
+        "algorithmic_flops_per_segment": flops / max(1, st["segments"]),
+        "overhead_flops_per_segment": overhead / max(1, st["segments"]),
+        "kernel_ms_per_step": ms / args.steps,
+        "share_of_step": ms / max(1e-9, head["dev_ms"])})
+    peaks = _peaks()
     formation = None
     if args.mode != "fp64" and kt["form_ms"] > 0:
         ff = alg_flops_formation(N_DIM, M_DIM, st["segments"])
         fa = ff / (kt["form_ms"] / 1e3) / 1e12
-        peaks = _peaks()
+        f64 = alg_flops_fp64_formation(N_DIM, M_DIM, st["segments"]) / (kt["form_ms"] / 1e3) / 1e12
         formation = {"bound": "tensor", "kernel": "ozaki_form_kernel (+ digit slicing)",
-                     "achieved": fa, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                     "frac": fa / peaks["bf16_tflops"], "peak_source": peaks["source"],
+                     "achieved": fa, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                     "frac": fa / peaks["bf16_tflops_sustained"],
+                     "peak_source": peaks["source"] + " (bf16, sustained)",
+                     "fp64_quality_tflops": f64, "fp64_quality_frac_of_fp64_peak":
+                         f64 / PEAK_FP64_TFLOPS,
                      "share_of_step": kt["form_ms"] / max(1e-9, head["dev_ms"])}
     contraction = None
     if args.mode != "fp64" and kt.get("contract_ms", 0) > 0:
         cf = alg_flops_contraction(N_DIM, M_DIM, st["segments"])
         ca = cf / (kt["contract_ms"] / 1e3) / 1e12
-        peaks = _peaks()
+        c64 = (alg_flops_fp64_contraction(N_DIM, M_DIM, st["reflections"])
+               / (kt["contract_ms"] / 1e3) / 1e12)
         contraction = {"bound": "tensor", "kernel": "ozaki_kernel<contract> (+ digit slicing)",
-                       "achieved": ca, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                       "frac": ca / peaks["bf16_tflops"], "peak_source": peaks["source"],
+                       "achieved": ca, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                       "frac": ca / peaks["bf16_tflops_sustained"],
+                       "peak_source": peaks["source"] + " (bf16, sustained)",
+                       "fp64_quality_tflops": c64,
                        "share_of_step": kt["contract_ms"] / max(1e-9, head["dev_ms"]),
                        "finish_share_of_step": kt["finish_ms"] / max(1e-9, head["dev_ms"])}
 
@@ -522,15 +626,21 @@ def main():
             import oracle
             oracle.build()
             for mode, r in list(context.items()) + [(args.mode, head)]:
-                checks[mode] = oracle_check(spectra, torch, spec, A, r["chains"], mode, 3)
+                if r["segments"] is not None:
+                    checks[mode] = oracle_check(A, r["segments"],
+                                                1e-10 if mode == "fp64" else 1e-9)
         except Exception as exc:
             checks = {"failed": str(exc)}
+    parity_pass = bool(checks) and all(isinstance(c, dict) and c.get("pass")
+                                       for c in checks.values())
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            r = cpu_oracle_rate(A, tau, chains=32, steps=1)
-            cpu = {k: r[k] for k in ["value", "unit", "cores", "kind", "sample"]}
+            wx, wstep = head["warm_state"]
+            r = cpu_oracle_rate(A, tau, wx, wstep, chains=32, steps=2)
+            cpu = {k: r[k] for k in ["value", "unit", "cores", "kind", "sample",
+                                     "segments_per_s"]}
         except Exception as exc:  # the baseline must not sink the GPU number
             cpu = {"value": None, "unit": "steps/s", "cores": None, "kind": "oracle",
                    "sample": "failed: %s" % exc}
@@ -539,6 +649,7 @@ def main():
         s = r["stats"]
         segs = max(1, s["segments"])
         return {"steps_per_s": C * r["steps"] / (r["dev_ms"] / 1e3),
+                "segments_per_s": s["segments"] / (r["dev_ms"] / 1e3),
                 "ms_per_step": r["dev_ms"] / r["steps"],
                 "segments_per_step": s["segments"] / (C * r["steps"]),
                 "iters_per_segment": s["lanczos_iters"] / segs,
@@ -569,6 +680,7 @@ def main():
                              "once before the timed steps",
                        "parallelism": "replicas x%d" % world},
             "oracle_calls_per_s": st["segments"] * world / (t_max / 1e3),
+            "parity_pass": parity_pass,
             "paths": paths,
             "speedup_vs_fp64": speedup,
             "oracle_check": checks,

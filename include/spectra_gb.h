@@ -50,6 +50,7 @@ extern "C" {
 #define SP_ST_NOCONV 3      /* Lanczos hit its cap; the result is the last Ritz value */
 #define SP_ST_RHO 4         /* Billiard: more than rho reflections, point kept (Alg. 5) */
 #define SP_ST_DEGENERATE 5  /* normal undefined: rank F(p+) <= m-2 (Lemma "Gradient of det F") */
+#define SP_ST_INVALID 6     /* a non-finite entry in the point or the direction (nothing computed) */
 
 /* arithmetic modes */
 #define SP_MODE_FP64 0   /* every step in FP64 */
@@ -57,8 +58,11 @@ extern "C" {
                             FP64 quality), FP32 estimate, double-float factorisation next to
                             the boundary and refinement of t+ and u (FP64 as the fallback);
                             needs n <= 224 (normals on the tensor cores: m <= 224) */
-#define SP_MODE_LEARNED 2  /* the mixed path with the network's warm start (sp_attach_mlp)
-                              for the Billiard walk; primitives run as SP_MODE_MIXED */
+#define SP_MODE_LEARNED 2  /* the mixed path with the network's warm start (sp_attach_mlp):
+                              the Billiard walk and sp_reflect start stage 1 from the
+                              network's prediction; sp_intersect (which also needs t-, not
+                              predicted) and the chord walks run as SP_MODE_MIXED; without
+                              an attached network SP_EINVAL */
 
 /* walk kinds (sp_chain_stats slots are SP_STAT_*) */
 #define SP_STAT_SEGMENTS 0     /* boundary-oracle calls */
@@ -114,7 +118,8 @@ int sp_membership(sp_spec* s, int count, const double* x, int* inside, void* str
  *   u       : device, count x m, or NULL: unit null vector of F(x + t+ v),
  *             largest-magnitude entry positive.
  *   status  : device int32, count (SP_ST_*).
- *   mode    : SP_MODE_FP64.
+ *   mode    : SP_MODE_FP64, SP_MODE_MIXED (t+ and t- to 1e-9 relative of the FP64
+ *             result) or SP_MODE_LEARNED (runs as SP_MODE_MIXED).
  */
 int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double* t_minus,
                  double* t_plus, double* u, int* status, int mode, void* stream);
@@ -126,6 +131,11 @@ int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double
  * into S), and the reflected direction s = v - 2 <v, w_hat> w_hat.
  *   x, v: device, count x n.  t_plus: device, count.  w_hat, s: device, count x n.
  *   status: device int32, count.
+ *   mode: SP_MODE_FP64, SP_MODE_MIXED or SP_MODE_LEARNED (the attached
+ *   network's warm start for stage 1; a prediction the factorisation or the
+ *   Lanczos test rejects falls back to the plain stage 1, so the results
+ *   meet the mixed path's accuracy either way; sp_learned_counts reports
+ *   the accepted and rejected warm starts of the last call).
  */
 int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* t_plus,
                double* w_hat, double* s_out, int* status, int mode, void* stream);
@@ -135,8 +145,9 @@ int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* 
  * F_out[c] = F(x_c) = A_0 + sum_i x_ci A_i and V_out[c] = sum_i v_ci A_i, as
  * packed lower triangles (count x m(m+1)/2, device).  x / F_out or v / V_out
  * may both be NULL.  SP_MODE_FP64: FP64 arithmetic.  SP_MODE_MIXED: BF16
- * tensor cores with exact digit splitting of both operands (49-bit digits,
- * FP64 result; error below (n+1) 2^-44 max_j |c_j| max_j |A_j[p]|).
+ * tensor cores with exact digit splitting of both operands (eight 7-bit
+ * digits, FP64 result; error below n 2^-51 max_j |c_j| max_{j>=1} |A_j[p]|
+ * plus one FP64 rounding).
  */
 int sp_form_pencil(sp_spec* s, int count, const double* x, const double* v, double* F_out,
                    double* V_out, int mode, void* stream);
@@ -224,7 +235,12 @@ int sp_chain_status(sp_chains* ch, int* status, long long* stats, void* stream);
  *   n, m     : dimension and matrix size.  m is limited to what one thread
  *              block's shared memory holds (about m <= 210), and the work
  *              space of at least one block must fit in the 8 MiB array;
- *              larger problems return SP_EINVAL.
+ *              larger problems return SP_EINVAL.  One block's work space is
+ *              m^2 + m(m+1)/2 + 96 m doubles, so the array holds
+ *              floor((2^20 - ceil(m(m+1)/4)) / that) blocks: 13 at m = 200,
+ *              52 at m = 100 (at most one per SM).  The call therefore runs
+ *              on that many SMs, well below the one block per SM of
+ *              sp_intersect for m above about 90.
  *   A_packed : device, (n+1) x m(m+1)/2 float64, caller-owned: row j is the
  *              lower triangle of A_j packed row by row (element (i, k), i >= k,
  *              at i(i+1)/2 + k).
@@ -290,6 +306,21 @@ int sp_attach_mlp(sp_spec* s, sp_mlp* q, double x_scale, double t_scale, double 
                   int iters);
 
 /*
+ * Diagnostic of the reciprocal routines inside the dense kernels (the
+ * Cholesky pivots and the inverted diagonal blocks use them instead of the
+ * FP64 divide and square root): for each x[c] (device, count float64)
+ * out[4c .. 4c+3] (device) = 1/sqrt(x) and 1/x from an FP32 seed refined by
+ * two Newton steps in FP64, then the same two in double-float arithmetic
+ * (rounded to FP64).  Valid for x in [1e-37, 3e37], the range the Cholesky
+ * accepts as pivots (outside it the factorisation reports failure).
+ */
+int sp_selftest_recip(int count, const double* x, double* out, void* stream);
+
+/* Warm starts accepted / rejected by the last SP_MODE_LEARNED sp_reflect call
+ * on `s` (host outputs, may be NULL; synchronises the device). */
+int sp_learned_counts(sp_spec* s, int* accepted, int* rejected);
+
+/*
  * Record training tuples during SP_MODE_MIXED / SP_MODE_LEARNED Billiard
  * walks: each segment whose refinement succeeded appends
  *   x_out[k] = (x * x_scale, v)          (2n floats),
@@ -299,6 +330,29 @@ int sp_attach_mlp(sp_spec* s, sp_mlp* q, double x_scale, double t_scale, double 
  * (defaults 1).  Pass x_out = NULL to stop recording.
  */
 int sp_record_tuples(sp_chains* ch, float* x_out, float* y_out, int capacity, int* count);
+
+/*
+ * Sampled record of the boundary-oracle calls (segments) of later walk calls
+ * on `ch` (all modes and walks; a measurement aid: what the walk's own
+ * Alg. 2 / Alg. 3 evaluations returned on the lines it actually visited).
+ * Every segment takes a ticket k from *count (device int32, zeroed by the
+ * caller, incremented once per segment); the segment is written to slot
+ * k / every when k % every == 0 and k / every < capacity.  buf (device,
+ * capacity x (3n + 8) float64) slot layout: p[n] (the start point of the
+ * segment), v[n] (its direction), w_hat[n] (unit normal, zeros unless the
+ * segment reflected), t_plus, t_minus (-inf for Billiard segments), status
+ * (SP_ST_*), reflected (1 if the walk reflected there), the chain's Philox
+ * index (chain0 + c), the step number, the segment's index within its
+ * step (0 for the first, i after i reflections) and the solver path as
+ * bit flags: 1 a shifted factorisation failed and a smaller shift was used,
+ * 2 the mixed path's stage 2 fell back to FP64, 4 / 8 the learned warm start
+ * was accepted / rejected, 16 an eigen-solve hit its cap, 32 a shift-invert
+ * refinement next to the boundary ran.  Slots fill in
+ * arrival order (not deterministic across runs).  buf = NULL stops
+ * recording.  SP_EINVAL when buf is given without count, capacity >= 1 and
+ * every >= 1.
+ */
+int sp_record_segments(sp_chains* ch, double* buf, int capacity, int every, int* count);
 
 /*
  * Per-kernel timing of later walk calls on `ch` (CUDA events recorded on the

@@ -101,6 +101,14 @@ def lib():
                                    ctypes.c_uint64, _i64p]
             L.orc_walk.restype = ctypes.c_int
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_billiard_trace.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                             ctypes.c_int, _dp, _dp, _i32p, _i32p]
+            L.orc_billiard_trace.restype = None
+            L.orc_reflect_batch.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                            _dp, _dp, _dp, _dp, _i32p, _dp]
+            L.orc_reflect_batch.restype = None
             _lib = L
     return _lib
 
@@ -263,6 +271,47 @@ def walk(kind: str, A, X, steps: int, *, tau: float = 1.0, rho: int = 100, kappa
                          kappa, seed, counts.ctypes.data_as(_i64p))
     return X, dict(segments=int(counts[0]), reflections=int(counts[1]),
                    bad_steps=int(counts[2]), errors=int(err))
+
+
+def billiard_trace(A, X, step: int, *, tau: float, rho: int = 100, kappa: float = 1e-6,
+                   seed: int = 0, chain0: int = 0, max_per_chain: int = 64):
+    """One Billiard step (Alg. 5) of every row of X (C x n, copied), recording
+    the line (p, v) of each segment the boundary oracle is called on.
+    Returns (X_new, P, V, status, rows): P and V are (K x n) stacks of the
+    recorded lines, in chain order (at most max_per_chain per chain), status
+    the per-chain step statuses, and rows a dict of per-row labels "chain"
+    (the Philox chain index chain0 + c) and "k" (index within the step)."""
+    A, n, m = _stack(A)
+    X = _f64(X).copy()
+    C = X.shape[0]
+    rp = np.zeros((C * max_per_chain, n))
+    rv = np.zeros((C * max_per_chain, n))
+    nseg = np.zeros(C, dtype=np.int32)
+    status = np.zeros(C, dtype=np.int32)
+    lib().orc_billiard_trace(n, m, _d(A), C, _d(X), step, chain0, tau, rho, kappa, seed,
+                             max_per_chain, _d(rp), _d(rv), nseg.ctypes.data_as(_i32p),
+                             status.ctypes.data_as(_i32p))
+    counts = [min(int(nseg[c]), max_per_chain) for c in range(C)]
+    keep = np.concatenate([np.arange(c * max_per_chain, c * max_per_chain + counts[c])
+                           for c in range(C)])
+    rows = {"chain": np.concatenate([np.full(counts[c], chain0 + c) for c in range(C)]),
+            "k": np.concatenate([np.arange(counts[c]) for c in range(C)])}
+    return X, rp[keep], rv[keep], status, rows
+
+
+def reflect_batch(A, P, V) -> dict:
+    """reflect() on every line (P[c], V[c]) (count x n each), in parallel."""
+    A, n, m = _stack(A)
+    P, V = _f64(P), _f64(V)
+    cnt = P.shape[0]
+    tp = np.zeros(cnt)
+    wh = np.zeros((cnt, n))
+    s = np.zeros((cnt, n))
+    st = np.zeros(cnt, dtype=np.int32)
+    info = np.zeros((cnt, 4))
+    lib().orc_reflect_batch(n, m, _d(A), cnt, _d(P), _d(V), _d(tp), _d(wh), _d(s),
+                            st.ctypes.data_as(_i32p), _d(info))
+    return dict(status=st, t_plus=tp, w_hat=wh, s=s, err_bar=info[:, 0], rel_gap=info[:, 1])
 
 
 def num_threads() -> int:

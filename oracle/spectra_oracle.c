@@ -539,9 +539,14 @@ out:
  *   x[n] is updated in place on success.  nrefl / nseg report the reflections
  *   and the boundary-oracle calls (segments) used.
  */
-int orc_billiard_step(int n, int m, const double* A, double* x, double tau, int rho,
-                      double kappa, uint64_t seed, uint32_t chain, uint32_t step,
-                      int* nrefl, int* nseg) {
+/* The Billiard step of Alg. 5 with an optional trace: when rec_p / rec_v are
+ * given, the line (p, v) of each of the first max_rec segments (the start
+ * point and direction that the boundary oracle is called on) is appended to
+ * them (max_rec x n each). */
+static int billiard_step_traced(int n, int m, const double* A, double* x, double tau, int rho,
+                                double kappa, uint64_t seed, uint32_t chain, uint32_t step,
+                                int* nrefl, int* nseg, double* rec_p, double* rec_v,
+                                int max_rec) {
   double* v = (double*)malloc(sizeof(double) * n);
   double* p = (double*)malloc(sizeof(double) * n);
   double* wh = (double*)malloc(sizeof(double) * n);
@@ -553,6 +558,10 @@ int orc_billiard_step(int n, int m, const double* A, double* x, double tau, int 
   int refl = 0, seg = 0, st = ORC_OK;
   for (;;) {
     double tp;
+    if (rec_p && seg < max_rec) {
+      memcpy(rec_p + (size_t)seg * n, p, sizeof(double) * n);
+      memcpy(rec_v + (size_t)seg * n, v, sizeof(double) * n);
+    }
     st = orc_reflect(n, m, A, p, v, &tp, wh, s, NULL);
     ++seg;
     if (st != ORC_OK) break;
@@ -575,6 +584,53 @@ int orc_billiard_step(int n, int m, const double* A, double* x, double tau, int 
   if (nseg) *nseg = seg;
   free(v); free(p); free(wh); free(s);
   return st;
+}
+
+int orc_billiard_step(int n, int m, const double* A, double* x, double tau, int rho,
+                      double kappa, uint64_t seed, uint32_t chain, uint32_t step,
+                      int* nrefl, int* nseg) {
+  return billiard_step_traced(n, m, A, x, tau, rho, kappa, seed, chain, step, nrefl, nseg, NULL,
+                              NULL, 0);
+}
+
+/*
+ * The lines the boundary oracle meets during one Billiard step (Alg. 5) of
+ * each of C chains: chain c (Philox chain index chain0 + c, step number
+ * `step`) starts at X[c] (updated in place, as orc_billiard_step) and appends
+ * the (p, v) of its first max_per_chain segments to rec_p / rec_v at rows
+ * c * max_per_chain + k (C * max_per_chain x n each); nseg[c] receives its
+ * number of segments (all of them, recorded or not) and status[c] the step's
+ * status.  Chains run in parallel (OpenMP) when built with it.
+ */
+void orc_billiard_trace(int n, int m, const double* A, int C, double* X, uint32_t step,
+                        uint32_t chain0, double tau, int rho, double kappa, uint64_t seed,
+                        int max_per_chain, double* rec_p, double* rec_v, int* nseg,
+                        int* status) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < C; ++c) {
+    int nr = 0, ns = 0;
+    status[c] = billiard_step_traced(n, m, A, X + (size_t)c * n, tau, rho, kappa, seed,
+                                     chain0 + (uint32_t)c, step, &nr, &ns,
+                                     rec_p + (size_t)c * max_per_chain * n,
+                                     rec_v + (size_t)c * max_per_chain * n, max_per_chain);
+    nseg[c] = ns;
+  }
+}
+
+/*
+ * orc_reflect on `count` independent lines (p_c, v_c) (rows of P and V,
+ * count x n): t_plus[c], w_hat (count x n), status[c] and info (count x 4, the
+ * per-line info of orc_intersect).  Lines run in parallel (OpenMP).
+ */
+void orc_reflect_batch(int n, int m, const double* A, int count, const double* P,
+                       const double* V, double* t_plus, double* w_hat, double* s, int* status,
+                       double* info) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < count; ++c) {
+    t_plus[c] = 0.0;
+    status[c] = orc_reflect(n, m, A, P + (size_t)c * n, V + (size_t)c * n, t_plus + c,
+                            w_hat + (size_t)c * n, s + (size_t)c * n, info + (size_t)c * 4);
+  }
 }
 
 /* One Hit-and-Run step (Alg. 4) with pi_l uniform on the chord:

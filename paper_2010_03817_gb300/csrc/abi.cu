@@ -126,6 +126,8 @@ struct MixSpace {
   double* Vrows = nullptr;    // rows x P
   int* err = nullptr;
   float2* vdf = nullptr;      // ctas x P: V as double-float pairs for stage 2
+  float* feats = nullptr;     // rows x 2n: warm-start features of the lines (learned reflect)
+  int* learned = nullptr;     // 2: warm starts accepted / rejected by the last learned call
   // deferred normals of a wave (tensor-core contraction)
   double* Ubuf = nullptr;     // rows x m
   double* Tbuf = nullptr;     // rows
@@ -137,7 +139,10 @@ struct MixSpace {
   void release() {
     cudaFree(Q32); cudaFree(Q64); cudaFree(region); cudaFree(digits); cudaFree(erow);
     cudaFree(Frows); cudaFree(Vrows); cudaFree(err); cudaFree(vdf);
+    cudaFree(feats); cudaFree(learned);
     vdf = nullptr;
+    feats = nullptr;
+    learned = nullptr;
     cudaFree(Ubuf); cudaFree(Tbuf); cudaFree(pend); cudaFree(Wpart); cudaFree(udig);
     cudaFree(uerow);
     Q32 = nullptr; Q64 = nullptr; region = nullptr; digits = nullptr; erow = nullptr;
@@ -269,8 +274,10 @@ struct sp_chains {
   int* done = nullptr;
   int* ids[2] = {nullptr, nullptr};
   double* dirs[2] = {nullptr, nullptr};
-  int* counts = nullptr;     // 2
+  int* counts = nullptr;     // 3: the two wave lists, the F refresh list
   int* h_count = nullptr;    // pinned host mirror
+  int* fage = nullptr;       // C: updates of each chain's carried F since its formation
+  int* ref_ids = nullptr;    // C: chains listed for a fresh formation of F
   float* feats = nullptr;    // C x 2n features of the learned path
   // optional per-kernel timing of walk calls (CUDA events on the walk's stream)
   bool timing = false;
@@ -278,6 +285,8 @@ struct sp_chains {
   double t_contract_ms = 0.0, t_finish_ms = 0.0;
   long long n_form = 0, n_wave = 0, n_mlp = 0, n_fp64 = 0, n_other = 0;
   long long n_contract = 0, n_finish = 0;
+  // sampled segment record (caller buffers, sp_record_segments)
+  SegLog seg{nullptr, 0, 1, nullptr};
   // tuple recording (caller buffers)
   float* rec_x = nullptr;
   float* rec_y = nullptr;
@@ -289,7 +298,10 @@ struct sp_chains {
     cudaFree(done); cudaFree(ids[0]); cudaFree(ids[1]); cudaFree(dirs[0]); cudaFree(dirs[1]);
     cudaFree(counts);
     cudaFree(feats);
+    cudaFree(fage);
+    cudaFree(ref_ids);
     feats = nullptr;
+    fage = ref_ids = nullptr;
     if (h_count) cudaFreeHost(h_count);
     F = Xstart = ell = tprev = nullptr;
     nrefl = done = counts = h_count = nullptr;
@@ -314,7 +326,7 @@ extern "C" {
 const char* sp_last_error(void) { return g_err.c_str(); }
 
 // error reporting for entry points defined in other translation units
-int sp_noalloc_error(int code, const char* msg) {
+int spg_set_error(int code, const char* msg) {
   g_err = msg;
   return code;
 }
@@ -487,14 +499,42 @@ static int form_rows_mixed(sp_spec* s, MixSpace& ms, int count, const double* x,
   return SP_OK;
 }
 
-static int run_prim_mixed(sp_spec* s, PrimParams& pp, void* stream) {
+static int run_prim_mixed(sp_spec* s, PrimParams& pp, bool learned, void* stream) {
   if (int r = check_mixed(s, "boundary oracle")) return r;
+  if (learned && !s->mlp)
+    return fail(SP_EINVAL, "boundary oracle: the learned mode needs a network (sp_attach_mlp)%s");
   const int ctas = std::min(pp.count, device_sms());
   int r = s->ms.ensure(s->n, s->m, std::max(ctas, 1), pp.count, s->kmax32, s->kmax64, true);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
   r = form_rows_mixed(s, s->ms, pp.count, pp.x, pp.v, s->ms.Frows, s->ms.Vrows, st);
   if (r) return r;
+  // learned warm start of REFLECTION: the network's (log t+, u) for every line
+  // (INTERSECTION also needs t-, which the network does not predict: it runs
+  // the plain mixed stage 1)
+  if (learned && pp.op == 1) {
+    MixSpace& ms = s->ms;
+    if (!ms.feats &&
+        (cudaMalloc(&ms.feats, sizeof(float) * (size_t)ms.rows * 2 * s->n) != cudaSuccess ||
+         cudaMalloc(&ms.learned, 2 * sizeof(int)) != cudaSuccess)) {
+      cudaGetLastError();
+      cudaFree(ms.feats);
+      ms.feats = nullptr;
+      return fail(SP_ENOMEM, "learned boundary oracle: feature buffer allocation failed%s");
+    }
+    cudaError_t e = launch_learned_features(pp.x, pp.v, nullptr, pp.count, s->n, s->x_scale,
+                                            ms.feats, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ms.learned, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "learned features");
+    const float* Y = nullptr;
+    int ld = 0;
+    if (int rr = spg_mlp_infer(s->mlp, pp.count, ms.feats, st, &Y, &ld)) return rr;
+    pp.pred = Y;
+    pp.ld_pred = ld;
+    pp.t_scale = s->t_scale;
+    pp.margin = s->margin;
+    pp.learned_ok = ms.learned;
+  }
   // reflect: the normals of all lines in one tensor-core contraction
   const bool tc_normals = pp.op == 1 && s->Bc != nullptr;
   if (tc_normals) {
@@ -553,7 +593,7 @@ int sp_intersect(sp_spec* s, int count, const double* x, const double* v, double
   pp.t_plus = t_plus;
   pp.u = u;
   pp.status = status;
-  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, stream);
+  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, false, stream);
   return run_prim(s, pp, stream);
 }
 
@@ -573,7 +613,7 @@ int sp_reflect(sp_spec* s, int count, const double* x, const double* v, double* 
   pp.w_hat = w_hat;
   pp.s = s_out;
   pp.status = status;
-  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, stream);
+  if (mode != SP_MODE_FP64) return run_prim_mixed(s, pp, mode == SP_MODE_LEARNED, stream);
   return run_prim(s, pp, stream);
 }
 
@@ -631,6 +671,30 @@ int sp_record_tuples(sp_chains* ch, float* x_out, float* y_out, int capacity, in
   ch->rec_y = y_out;
   ch->rec_count = count;
   ch->rec_cap = x_out ? capacity : 0;
+  return SP_OK;
+}
+
+int sp_learned_counts(sp_spec* s, int* accepted, int* rejected) {
+  if (!s) return fail(SP_EINVAL, "sp_learned_counts: null handle%s");
+  int h[2] = {0, 0};
+  if (s->ms.learned) {
+    if (cudaMemcpy(h, s->ms.learned, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "sp_learned_counts");
+  }
+  if (accepted) *accepted = h[0];
+  if (rejected) *rejected = h[1];
+  return SP_OK;
+}
+
+int sp_record_segments(sp_chains* ch, double* buf, int capacity, int every, int* count) {
+  if (!ch) return fail(SP_EINVAL, "sp_record_segments: null handle%s");
+  if (buf && (!count || capacity < 1 || every < 1))
+    return fail(SP_EINVAL, "sp_record_segments: buffer, capacity >= 1, every >= 1 and counter "
+                           "go together%s");
+  ch->seg.buf = buf;
+  ch->seg.cap = buf ? capacity : 0;
+  ch->seg.every = buf ? every : 1;
+  ch->seg.count = buf ? count : nullptr;
   return SP_OK;
 }
 
@@ -758,7 +822,9 @@ static int ensure_chain_mixed(sp_chains* ch) {
             cudaMalloc(&ch->ids[1], sizeof(int) * C) == cudaSuccess &&
             cudaMalloc(&ch->dirs[0], sizeof(double) * (size_t)C * n) == cudaSuccess &&
             cudaMalloc(&ch->dirs[1], sizeof(double) * (size_t)C * n) == cudaSuccess &&
-            cudaMalloc(&ch->counts, 2 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ch->counts, 3 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ch->fage, sizeof(int) * C) == cudaSuccess &&
+            cudaMalloc(&ch->ref_ids, sizeof(int) * C) == cudaSuccess &&
             cudaMallocHost(&ch->h_count, sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -789,9 +855,13 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
   }
   cudaStream_t st = (cudaStream_t)stream;
   const DevSpec ds = s->dev();
-  if (!ch->F_valid) {
+  {
+    // F(x) of every chain formed afresh at the start of each call; within the
+    // call it is carried (F <- F + t V) and re-formed after kFRefresh updates
     cudaError_t e = launch_ozaki_form(ch->X, ch->C, s->n, 1.0, s->A, s->Bsl, s->ecol, s->P,
                                       ch->ms.digits, ch->ms.erow, ch->F, s->P, ch->ms.err, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ch->fage, 0, sizeof(int) * ch->C, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ch->counts + 2, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core formation (F)");
     ch->F_valid = true;
   }
@@ -824,6 +894,10 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
   wv.rec_y = ch->rec_y;
   wv.rec_count = ch->rec_count;
   wv.rec_cap = ch->rec_cap;
+  wv.seg = ch->seg;
+  wv.fage = ch->fage;
+  wv.ref_ids = ch->ref_ids;
+  wv.ref_count = ch->counts + 2;
   // Billiard: the reflections' normals on the tensor cores, one contraction
   // per wave (deferred from the wave kernel to a finish kernel)
   const bool defer = kind == 0 && s->Bc != nullptr;
@@ -860,11 +934,22 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
     wv.count_next = ch->counts + (cur ^ 1);
     e = cudaMemsetAsync(wv.count_next, 0, sizeof(int), st);
     if (ch->timing) cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess)
+    // V of every listed chain on the tensor cores (CDHR reads V = A_j from
+    // the stack instead)
+    if (e == cudaSuccess && kind != 2) {
       e = launch_ozaki_form(wv.dir_cur, count, s->n, 0.0, s->A, s->Bsl, s->ecol, s->P, ch->ms.digits,
                             ch->ms.erow, ch->ms.Vrows, s->P, ch->ms.err, st);
+      ch->n_form += 2;  // digit slicing + tensor-core formation
+    }
+    // fresh F(x) of the chains the last wave listed (at most this wave's
+    // chains; the list's length is on the device), written into their
+    // carried F; then the list starts over for this wave
+    if (e == cudaSuccess)
+      e = launch_ozaki_form(ch->X, count, s->n, 1.0, s->A, s->Bsl, s->ecol, s->P, ch->ms.digits,
+                            ch->ms.erow, ch->F, s->P, ch->ms.err, st, ch->ref_ids, ch->counts + 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ch->counts + 2, 0, sizeof(int), st);
+    ch->n_form += 2;
     if (ch->timing) cudaEventRecord(ev[1], st);
-    ch->n_form += 2;  // digit slicing + tensor-core formation
     if (e == cudaSuccess && learned && kind == 0) {
       // warm start: the network's (log t+, u) for every listed chain
       e = launch_learned_features(ch->X, wv.dir_cur, wv.id_cur, count, s->n, s->x_scale,
@@ -953,6 +1038,7 @@ static int run_walk(sp_chains* ch, int kind, int steps, double tau, int rho, dou
   wp.X = ch->X;
   wp.status = ch->status;
   wp.stats = ch->stats;
+  wp.seg = ch->seg;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ch->timing) {
     cudaEventCreate(&e0);

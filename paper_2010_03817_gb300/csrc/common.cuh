@@ -117,6 +117,47 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return s;
 }
 
+// CTA-wide: the slot of the calling segment in a sampled segment record, or -1
+// (thread 0 takes the ticket; `ib` is a shared int used for the broadcast)
+template <typename Log>
+__device__ __forceinline__ int seglog_slot(const Log& lg, int* ib) {
+  if (!lg.buf) return -1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int k = atomicAdd(lg.count, 1);
+    *ib = (k % lg.every == 0 && k / lg.every < lg.cap) ? k / lg.every : -1;
+  }
+  __syncthreads();
+  const int slot = *ib;
+  __syncthreads();
+  return slot;
+}
+
+// CTA-wide: write one segment record (layout of SegLog in kernels.h)
+template <typename Log>
+__device__ __forceinline__ void seglog_write(const Log& lg, int slot, int n, const double* p,
+                                             const double* v, const double* wh, double t_plus,
+                                             double t_minus, int status, int reflected,
+                                             uint32_t chain, uint32_t step, int kseg,
+                                             int flags) {
+  double* r = lg.buf + (size_t)slot * (3 * (size_t)n + 8);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    r[j] = p[j];
+    r[n + j] = v[j];
+    r[2 * n + j] = wh ? wh[j] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    r[3 * n] = t_plus;
+    r[3 * n + 1] = t_minus;
+    r[3 * n + 2] = (double)status;
+    r[3 * n + 3] = (double)reflected;
+    r[3 * n + 4] = (double)chain;
+    r[3 * n + 5] = (double)step;
+    r[3 * n + 6] = (double)kseg;
+    r[3 * n + 7] = (double)flags;
+  }
+}
+
 // packed lower triangle, row-major: element (i, k), i >= k
 __host__ __device__ __forceinline__ size_t tri(int i, int k) {
   return (size_t)i * (size_t)(i + 1) / 2 + (size_t)k;

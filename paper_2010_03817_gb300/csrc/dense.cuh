@@ -411,4 +411,33 @@ __device__ void mul_upper(const T* L, const T* x, T* y, int m, T* part) {
   __syncthreads();
 }
 
+// Pencil Rayleigh correction of a root t0 of det(F + tV) with null-vector
+// estimate u (CTA-wide, FP64):
+//   t = t0 - u^T (F + t0 V) u / (u^T V u),
+// the Newton step of the Rayleigh quotient t(u) = -(u^T F u)/(u^T V u),
+// which is stationary at the null vector: its error is quadratic in the
+// error of u, and it is evaluated on the exact FP64 F and V instead of
+// through a factorisation, so the factorisation's backward error (about
+// m eps |F|, large when |F| >> |u^T F u|) does not enter t.  F: packed
+// lower triangle (global or shared); V: packed (vfull = false) or full
+// m x m row-major (vfull = true); pidx: (i << 16) | k per packed entry; u:
+// shared, m; red: SPG_WARPS doubles.  Returns NaN if u^T V u == 0.
+__device__ inline double pencil_correct(const double* __restrict__ F, const double* __restrict__ V,
+                                        bool vfull, int m, long long P,
+                                        const uint32_t* __restrict__ pidx, const double* u,
+                                        double t0, double* red) {
+  double a = 0.0, b = 0.0;
+  for (long long e = threadIdx.x; e < P; e += SPG_THREADS) {
+    const uint32_t ik = pidx[e];
+    const int i = ik >> 16, k = ik & 0xffff;
+    const double ve = vfull ? V[(size_t)i * m + k] : V[e];
+    const double uu = (i == k ? 1.0 : 2.0) * (u[i] * u[k]);
+    a = fma(fma(t0, ve, F[e]), uu, a);
+    b = fma(ve, uu, b);
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  return b != 0.0 ? t0 - a / b : NAN;
+}
+
 }  // namespace spg

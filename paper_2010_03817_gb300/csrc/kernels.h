@@ -22,6 +22,7 @@ enum ChainStatus : int {
   kNoConv = 3,
   kRho = 4,
   kDegenerate = 5,
+  kInvalid = 6,
 };
 
 // per-chain statistics slots (int64 each)
@@ -37,6 +38,30 @@ enum StatSlot : int {
   kStatLearnedOk = 8,    // learned path: warm starts accepted by the certificate
   kStatLearnedMiss = 9,  // learned path: warm starts rejected (plain stage 1 instead)
   kNumStats = 12,
+};
+
+// Sampled record of the boundary-oracle calls of a walk (sp_record_segments):
+// the k-th segment any chain completes (arrival order, one atomic ticket per
+// segment) is written to slot k / every when k % every == 0 and k / every <
+// cap.  Slot layout (3n + 8 doubles): p[n] (start of the segment), v[n]
+// (direction), w_hat[n] (unit normal, zero unless the segment reflected),
+// t_plus, t_minus (-inf unless computed), status, reflected (0 / 1), the
+// chain's Philox index, the step number, the segment's index in its step
+// and the solver path flags (kSegFlag*).
+struct SegLog {
+  double* buf;  // cap x (3n + 8), or null: no recording
+  int cap;
+  int every;
+  int* count;   // segments seen so far (device)
+};
+constexpr int kSegExtra = 8;
+enum SegFlag : int {
+  kSegShiftRetry = 1,     // the shifted factorisation failed: a smaller shift was used
+  kSegFallback = 2,       // mixed path: stage 2 fell back to FP64
+  kSegLearnedOk = 4,      // learned path: the warm start was accepted
+  kSegLearnedMiss = 8,    // learned path: the warm start was rejected
+  kSegNoConv = 16,        // an eigen-solve hit its iteration cap
+  kSegRefined = 32,       // a shift-invert refinement next to the boundary ran
 };
 
 struct DevSpec {
@@ -69,6 +94,7 @@ struct WalkParams {
   double* X;         // C x n
   int* status;       // C
   long long* stats;  // C x kNumStats
+  SegLog seg;
 };
 
 struct PrimParams {
@@ -88,6 +114,11 @@ struct PrimParams {
   double* Ubuf;
   const double* Wpart;
   int wtiles;
+  // learned warm start (reflect): the network's (log(t+ / t_scale), u) per line
+  const float* pred;
+  int ld_pred;
+  double t_scale, margin;
+  int* learned_ok;  // optional device pair: warm starts accepted / rejected
 };
 
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem);
@@ -145,7 +176,16 @@ struct MixWave {
   int* pend;
   const double* Wpart;  // slot x (n+1) x wtiles partial sums of w_j
   int wtiles;
+  SegLog seg;
+  // F refresh: a chain whose carried F has taken kFRefresh updates (or whose
+  // step was rejected) is listed for a fresh formation before the next wave
+  int* fage;        // C updates since the last fresh formation
+  int* ref_ids;     // chains listed for the next wave's formation of F
+  int* ref_count;
 };
+// updates of a carried F between fresh formations: Billiard and Hit-and-Run,
+// CDHR (whose update F + t A_j the paper prescribes)
+constexpr int kFRefresh = 16, kFRefreshCdhr = 64;
 
 size_t mixed_region_bytes(int n, int m);
 cudaError_t launch_learned_features(const double* X, const double* dir, const int* id, int count,
@@ -169,9 +209,12 @@ int ozaki_kp(int n);
 size_t ozaki_b_bytes(long long P, int n);
 size_t ozaki_row_bytes(int R, int n);
 void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol);
+// rows (optional): coefficient row r is vec[rows[r]] and its result goes to
+// Y[rows[r]]; count_dev (optional, device): only rows r < *count_dev
 cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const double* A0,
                               const uint16_t* Bsl, const int* ecol, long long P, void* row_digits,
-                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st);
+                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st,
+                              const int* rows = nullptr, const int* count_dev = nullptr);
 constexpr int kOzakiMaxK = 224;  // n limit of the tensor-core formation (m for the contraction)
 // the normal forms w_j = u^T A_j u of R null vectors on the tensor cores:
 // (A_j u)_i by the same digit-split GEMM over the rows (j, i) of the full

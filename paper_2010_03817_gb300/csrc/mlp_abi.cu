@@ -14,11 +14,11 @@
 
 using namespace spg;
 
-extern "C" int sp_noalloc_error(int code, const char* msg);
+extern "C" int spg_set_error(int code, const char* msg);
 
 namespace {
 
-int mlp_fail(int code, const char* msg) { return sp_noalloc_error(code, msg); }
+int mlp_fail(int code, const char* msg) { return spg_set_error(code, msg); }
 
 inline int round8(int x) { return (x + 7) / 8 * 8; }
 inline int round16(int x) { return (x + 15) / 16 * 16; }

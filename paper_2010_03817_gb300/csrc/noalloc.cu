@@ -41,19 +41,19 @@ __global__ void fill_pair_index(uint32_t* pidx, int m) {
 
 }  // namespace
 
-extern "C" int sp_noalloc_error(int code, const char* msg);  // defined in abi.cu
+extern "C" int spg_set_error(int code, const char* msg);  // defined in abi.cu
 
 extern "C" int sp_intersect_noalloc(int n, int m, const double* A_packed, int count,
                                     const double* x, const double* v, double* t_minus,
                                     double* t_plus, int* status, void* stream) {
   if (n < 1 || m < 1 || m > 4096 || count < 0)
-    return sp_noalloc_error(SP_EINVAL, "sp_intersect_noalloc: bad n, m or count");
+    return spg_set_error(SP_EINVAL, "sp_intersect_noalloc: bad n, m or count");
   if (count == 0) return SP_OK;
   if (!A_packed || !x || !v || !t_minus || !t_plus || !status)
-    return sp_noalloc_error(SP_EINVAL, "sp_intersect_noalloc: null argument");
+    return spg_set_error(SP_EINVAL, "sp_intersect_noalloc: null argument");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return sp_noalloc_error(SP_ECUDA, "sp_intersect_noalloc: no current device");
+    return spg_set_error(SP_ECUDA, "sp_intersect_noalloc: no current device");
   double* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -62,7 +62,7 @@ extern "C" int sp_intersect_noalloc(int n, int m, const double* A_packed, int co
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) {
         cudaGetLastError();
-        return sp_noalloc_error(SP_ECUDA, "sp_intersect_noalloc: scratch address lookup failed");
+        return spg_set_error(SP_ECUDA, "sp_intersect_noalloc: scratch address lookup failed");
       }
       g_scratch_addr[dev] = static_cast<double*>(p);
     }
@@ -73,13 +73,13 @@ extern "C" int sp_intersect_noalloc(int n, int m, const double* A_packed, int co
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (spg::fp64_smem_bytes(n, m, true) > (size_t)optin)
-    return sp_noalloc_error(SP_EINVAL, "sp_intersect_noalloc: m too large for this entry point");
+    return spg_set_error(SP_EINVAL, "sp_intersect_noalloc: m too large for this entry point");
   const long long P = (long long)m * (m + 1) / 2;
   const int kmax = 96;
   const size_t pidx_doubles = (size_t)(P + 1) / 2;
   const size_t per_cta = (size_t)m * m + (size_t)P + (size_t)kmax * m;
   if (pidx_doubles + per_cta > kScratchDoubles)
-    return sp_noalloc_error(SP_EINVAL,
+    return spg_set_error(SP_EINVAL,
                             "sp_intersect_noalloc: problem exceeds the 8 MiB static scratch");
   int ctas = (int)((kScratchDoubles - pidx_doubles) / per_cta);
   if (ctas > sms) ctas = sms;
@@ -90,7 +90,7 @@ extern "C" int sp_intersect_noalloc(int n, int m, const double* A_packed, int co
   fill_pair_index<<<m < 1024 ? m : 1024, 128, 0, st>>>(pidx, m);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
-    return sp_noalloc_error(SP_ECUDA, "sp_intersect_noalloc: index kernel launch failed");
+    return spg_set_error(SP_ECUDA, "sp_intersect_noalloc: index kernel launch failed");
   spg::DevSpec sp;
   sp.n = n;
   sp.m = m;
@@ -117,6 +117,6 @@ extern "C" int sp_intersect_noalloc(int n, int m, const double* A_packed, int co
   pp.status = status;
   e = spg::launch_prim_fp64(sp, wk, pp, st);
   if (e != cudaSuccess)
-    return sp_noalloc_error(SP_ECUDA, "sp_intersect_noalloc: kernel launch failed");
+    return spg_set_error(SP_ECUDA, "sp_intersect_noalloc: kernel launch failed");
   return SP_OK;
 }

@@ -13,16 +13,17 @@
 // tensor-core form, Mukunoki, Ozaki, Ogita, Imamura 2020):
 //   c_r[j] = 2^{f_r} sum_s a_s[r, j] 2^{-7(s+1)},  A[j, p] = 2^{e_p} sum_t b_t[j, p] 2^{-7(t+1)}
 // (j = 1..n)
-// with integer digits |a_s|, |b_t| <= 64 (exact in BF16), S = 7 digits (49
-// bits).  For each digit-sum d = s + t <= 6 the tensor core accumulates
+// with integer digits |a_s|, |b_t| <= 64 (exact in BF16), S digits (7S bits:
+// S = 8 for the formation, 7 for the normal contraction).  For each digit sum
+// d = s + t <= S - 1 the tensor core accumulates
 //   G_d[r, p] = sum_{s+t=d} sum_j a_s[r, j] b_t[j, p]
-// in FP32 in TMEM; every partial sum is an integer below 7 * 224 * 2^12 < 2^24,
-// so the accumulation is exact.  The epilogue combines the seven integers in
-// 64-bit integer arithmetic and scales once into FP64:
+// in FP32 in TMEM; every partial sum is an integer below S * 224 * 2^12 <
+// 2^24, so the accumulation is exact.  The epilogue combines the S integers
+// in 64-bit integer arithmetic and scales once into FP64:
 //   Y = 2^{f_r + e_p} sum_d G_d 2^{-7(d+2)}.
-// The truncation (pairs with s + t > 6, digits beyond the 7th) is below
-// n 2^-44 max_j |c_r[j]| max_{j>=1} |A[j, p]|, plus one FP64 rounding of the
-// sum with lead A_0[p].
+// The truncation (pairs with s + t > S - 1, digits beyond the S-th) is below
+// n 2^{-(7S - 5)} max_j |c_r[j]| max_{j>=1} |A[j, p]| (2^-51 for S = 8), plus
+// one FP64 rounding of the sum with lead A_0[p].
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -33,11 +34,12 @@
 namespace spg {
 namespace {
 
-constexpr int kDigits = 7;        // S
-constexpr int kDigitBits = 7;     // beta
-constexpr int kTileM = 128;       // coefficient rows per CTA
-constexpr int kTileN = 32;        // packed entries per CTA
-constexpr int kGroups = kDigits;  // d = 0..6
+constexpr int kFormDigits = 8;      // S of the pencil formation (F and V)
+constexpr int kContractDigits = 7;  // S of the normal contraction
+constexpr int kMaxDigits = 8;
+constexpr int kDigitBits = 7;       // beta
+constexpr int kTileM = 128;         // coefficient rows per CTA
+constexpr int kTileN = 32;          // packed entries per CTA
 constexpr int kThreads = 128;
 
 __device__ __forceinline__ uint32_t core_off(int r, int g, int kgroups) {
@@ -75,13 +77,16 @@ __device__ __forceinline__ double i128_to_double(__int128 T, int scale) {
                                           (mant & 0xfffffffffffffull)));
 }
 
-// one warp per row: exponent and digits of c_r = vec[r, 0..n-1]
+// one warp per row: exponent and ND digits of c_r = vec[rows[r], 0..n-1]
+// (rows null: vec[r]); rows r >= *count_dev are skipped when count_dev is given
+template <int ND>
 __global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, int Kp,
-                                  __nv_bfloat16* __restrict__ out, int* __restrict__ ex) {
+                                  __nv_bfloat16* __restrict__ out, int* __restrict__ ex,
+                                  const int* __restrict__ rows, const int* __restrict__ count_dev) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= R) return;
-  const double* row = vec + (size_t)r * n;
+  if (r >= R || (count_dev && r >= *count_dev)) return;
+  const double* row = vec + (size_t)(rows ? rows[r] : r) * n;
   double mx = 0.0;
   for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(row[j]));
   mx = warp_max(mx);
@@ -94,7 +99,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ vec, int R, int n, 
   for (int k = lane; k < Kp; k += 32) {
     double y = k < n ? ldexp(row[k], -e) : 0.0;
 #pragma unroll
-    for (int s = 0; s < kDigits; ++s) {
+    for (int s = 0; s < ND; ++s) {
       y *= 128.0;
       const double d = rint(y);
       y -= d;
@@ -115,18 +120,29 @@ struct OzEpi {
   double lead;
   double* Y;
   long long ldy;
+  const int* rows;       // formation: output row of coefficient row r (null: r)
+  const int* count_dev;  // formation: rows r >= *count_dev are skipped (null: R)
   const double* U;
   int m, mpad, n1;
   double* Wpart;
 };
 
-template <int kMode>
+template <int kMode, int kDigits>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_kernel(const __nv_bfloat16* __restrict__ Asl, const int* __restrict__ erow, int R,
                  const __nv_bfloat16* __restrict__ Bsl, const int* __restrict__ ecol, long long P,
                  int Kp, OzEpi ep, int* err) {
+  constexpr int kGroups = kDigits;  // digit sums d = 0..kDigits-1
+  static_assert(kGroups * kTileN <= 256, "the digit sums must fit the 256 TMEM columns");
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // a device-side row count (formation of a list built on the GPU): blocks
+  // past it leave before touching the tensor memory
+  if (kMode == kForm && ep.count_dev) {
+    const int rl = *ep.count_dev;
+    R = rl < R ? rl : R;
+  }
+  if ((kMode == kForm ? (int)blockIdx.y : (int)blockIdx.x) * kTileM >= R) return;
   const int kgroups = Kp / 8;
   const uint32_t a_bytes = kTileM * Kp * 2;
   const uint32_t b_bytes = kTileN * Kp * 2;
@@ -271,29 +287,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int d = 0; d < kGroups; ++d) tc::tmem_ld16(lane_base + (uint32_t)(d * kTileN + c0), v[d]);
       tc::tmem_wait_ld();
+      // hi carries the digit sums d < kHi, lo the rest (Horner in base 2^7,
+      // each below 2^(24 + 7 (kHi - 1)) < 2^63):
+      //   value = 2^(e - 7 (kDigits + 1)) (hi 2^(7 (kDigits - kHi)) + lo),
+      // one rounding (integer operations)
+      constexpr int kHi = 4;
+      constexpr int kLoShift = kDigitBits * (kDigits - kHi);
+      constexpr int kScale = kDigitBits * (kDigits + 1);
 #pragma unroll
       for (int d = 0; d < kGroups; ++d) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           // exact integers below 2^24 in magnitude
           const long long g = (long long)__float2int_rn(__uint_as_float(v[d][i]));
-          if (d <= 3)
+          if (d < kHi)
             hi[i] = hi[i] * (1ll << kDigitBits) + g;
           else
             lo[i] = lo[i] * (1ll << kDigitBits) + g;
         }
       }
       if (r < R) {
-        // hi carries digit sums d = 0..3, lo d = 4..6:
-        //   value = 2^(e - 56) (hi 2^21 + lo), one rounding (integer ops)
         if (kMode == kForm) {
-          double* yrow = ep.Y + (size_t)r * ep.ldy;
+          double* yrow = ep.Y + (size_t)(ep.rows ? ep.rows[r] : r) * ep.ldy;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const long long p = p0 + c0 + i;
             if (p < P) {
-              const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
-                                              er + ec[i] - 56);
+              const double y = i128_to_double(((__int128)hi[i] << kLoShift) + (__int128)lo[i],
+                                              er + ec[i] - kScale);
               yrow[p] = ep.lead != 0.0 ? fma(ep.lead, aux[i], y) : y;
             }
           }
@@ -301,8 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             if (i0 + c0 + i < ep.m) {
-              const double y = i128_to_double(((__int128)hi[i] << 21) + (__int128)lo[i],
-                                              er + ec[i] - 56);
+              const double y = i128_to_double(((__int128)hi[i] << kLoShift) + (__int128)lo[i],
+                                              er + ec[i] - kScale);
               part = fma(y, aux[i], part);
             }
           }
@@ -342,7 +363,7 @@ __global__ void slice_full_kernel(const double* __restrict__ A, int n1, int m, l
   for (int k = lane; k < Kp; k += 32) {
     double y = (i < m && k < m) ? ldexp(Aj[i >= k ? tri(i, k) : tri(k, i)], -e) : 0.0;
 #pragma unroll
-    for (int s = 0; s < kDigits; ++s) {
+    for (int s = 0; s < kContractDigits; ++s) {
       y *= 128.0;
       const double d = rint(y);
       y -= d;
@@ -351,15 +372,17 @@ __global__ void slice_full_kernel(const double* __restrict__ A, int n1, int m, l
   }
 }
 
-inline size_t ozaki_smem(int Kp) {
-  return (size_t)kDigits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
+inline size_t ozaki_smem(int Kp, int digits) {
+  return (size_t)digits * kTileN * Kp * 2 + 2 * (size_t)kTileM * Kp * 2 + 64;
 }
 
 }  // namespace
 
 int ozaki_kp(int n) { return (n + 15) / 16 * 16; }
 
-size_t ozaki_b_bytes(long long P, int n) { return (size_t)kDigits * (size_t)P * ozaki_kp(n) * 2; }
+size_t ozaki_b_bytes(long long P, int n) {
+  return (size_t)kFormDigits * (size_t)P * ozaki_kp(n) * 2;
+}
 
 // host: digits of A_1..A_n, column by column (packed entry p over j = 1..n)
 void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, int* ecol) {
@@ -375,7 +398,7 @@ void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, 
     ecol[p] = e;
     for (int k = 0; k < Kp; ++k) {
       double y = (k < n) ? ldexp(packed[(size_t)(k + 1) * P + p], -e) : 0.0;
-      for (int s = 0; s < kDigits; ++s) {
+      for (int s = 0; s < kFormDigits; ++s) {
         y *= 128.0;
         const double d = rint(y);
         y -= d;
@@ -389,28 +412,32 @@ void ozaki_slice_stack(const double* packed, int n, long long P, uint16_t* Bsl, 
   }
 }
 
-size_t ozaki_row_bytes(int R, int n) { return (size_t)kDigits * R * ozaki_kp(n) * 2; }
+size_t ozaki_row_bytes(int R, int n) { return (size_t)kMaxDigits * R * ozaki_kp(n) * 2; }
 
 cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, const double* A0,
                               const uint16_t* Bsl, const int* ecol, long long P, void* row_digits,
-                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st) {
+                              int* erow, double* Y, long long ldy, int* err, cudaStream_t st,
+                              const int* rows, const int* count_dev) {
   if (R <= 0) return cudaSuccess;
   const int Kp = ozaki_kp(n);
   __nv_bfloat16* Asl = static_cast<__nv_bfloat16*>(row_digits);
-  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, Kp, Asl, erow);
+  slice_rows_kernel<kFormDigits><<<(R + 7) / 8, 256, 0, st>>>(vec, R, n, Kp, Asl, erow, rows,
+                                                               count_dev);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = ozaki_smem(Kp);
-  e = cudaFuncSetAttribute(ozaki_kernel<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  const size_t smem = ozaki_smem(Kp, kFormDigits);
+  e = cudaFuncSetAttribute(ozaki_kernel<kForm, kFormDigits>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   OzEpi ep{};
   ep.A0 = A0;
   ep.lead = lead;
   ep.Y = Y;
   ep.ldy = ldy;
+  ep.rows = rows;
+  ep.count_dev = count_dev;
   dim3 grid((unsigned)((P + kTileN - 1) / kTileN), (unsigned)((R + kTileM - 1) / kTileM));
-  ozaki_kernel<kForm><<<grid, kThreads, smem, st>>>(
+  ozaki_kernel<kForm, kFormDigits><<<grid, kThreads, smem, st>>>(
       Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bsl), ecol, P, Kp, ep, err);
   return cudaGetLastError();
 }
@@ -418,7 +445,7 @@ cudaError_t launch_ozaki_form(const double* vec, int R, int n, double lead, cons
 int ozaki_mpad(int m) { return (m + kTileN - 1) / kTileN * kTileN; }
 
 size_t ozaki_contract_bytes(int n, int m) {
-  return (size_t)kDigits * (size_t)(n + 1) * ozaki_mpad(m) * ozaki_kp(m) * 2;
+  return (size_t)kContractDigits * (size_t)(n + 1) * ozaki_mpad(m) * ozaki_kp(m) * 2;
 }
 
 cudaError_t launch_ozaki_slice_full(const double* A, int n, int m, long long P, uint16_t* Bc,
@@ -435,12 +462,13 @@ cudaError_t launch_ozaki_contract(const double* U, int R, int n, int m, const ui
   if (R <= 0) return cudaSuccess;
   const int Kp = ozaki_kp(m), mpad = ozaki_mpad(m);
   __nv_bfloat16* Asl = static_cast<__nv_bfloat16*>(row_digits);
-  slice_rows_kernel<<<(R + 7) / 8, 256, 0, st>>>(U, R, m, Kp, Asl, erow);
+  slice_rows_kernel<kContractDigits><<<(R + 7) / 8, 256, 0, st>>>(U, R, m, Kp, Asl, erow,
+                                                                   nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = ozaki_smem(Kp);
-  e = cudaFuncSetAttribute(ozaki_kernel<kContract>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  const size_t smem = ozaki_smem(Kp, kContractDigits);
+  e = cudaFuncSetAttribute(ozaki_kernel<kContract, kContractDigits>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   OzEpi ep{};
   ep.U = U;
@@ -450,7 +478,7 @@ cudaError_t launch_ozaki_contract(const double* U, int R, int n, int m, const ui
   ep.Wpart = Wpart;
   const long long Q = (long long)(n + 1) * mpad;
   dim3 grid((unsigned)((R + kTileM - 1) / kTileM), (unsigned)(Q / kTileN));
-  ozaki_kernel<kContract><<<grid, kThreads, smem, st>>>(
+  ozaki_kernel<kContract, kContractDigits><<<grid, kThreads, smem, st>>>(
       Asl, erow, R, reinterpret_cast<const __nv_bfloat16*>(Bc), ecolc, Q, Kp, ep, err);
   return cudaGetLastError();
 }

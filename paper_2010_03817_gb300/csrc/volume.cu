@@ -20,7 +20,7 @@
 #include "common.cuh"
 #include "kernels.h"
 
-extern "C" int sp_noalloc_error(int code, const char* msg);  // defined in abi.cu
+extern "C" int spg_set_error(int code, const char* msg);  // defined in abi.cu
 
 namespace spg {
 namespace {
@@ -52,10 +52,10 @@ extern "C" {
 int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio, int chains,
                        int burn_in, int steps, int walk, int mode, uint64_t seed, double* vol,
                        double* info, void* stream) {
-  if (!s || !vol) return sp_noalloc_error(SP_EINVAL, "sp_volume_estimate: null argument");
+  if (!s || !vol) return spg_set_error(SP_EINVAL, "sp_volume_estimate: null argument");
   if (!(r_inner > 0.0) || !(r_outer > r_inner) || !(ratio > 0.0 && ratio < 1.0) || chains < 1 ||
       burn_in < 0 || steps < 1 || (walk != 0 && walk != 1))
-    return sp_noalloc_error(SP_EINVAL, "sp_volume_estimate: bad radii, ratio or counts");
+    return spg_set_error(SP_EINVAL, "sp_volume_estimate: bad radii, ratio or counts");
   const auto t0 = std::chrono::steady_clock::now();
   int n = 0, m = 0;
   if (int r = sp_spec_dims(s, &n, &m)) return r;
@@ -70,7 +70,7 @@ int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio,
   unsigned long long* dcount = nullptr;
   if (cudaMalloc(&dcount, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
-    return sp_noalloc_error(SP_ENOMEM, "sp_volume_estimate: allocation failed");
+    return spg_set_error(SP_ENOMEM, "sp_volume_estimate: allocation failed");
   }
   double log_vol = spg::log_ball_volume(n, r_inner);
   double rel_var = 0.0;
@@ -103,7 +103,7 @@ int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio,
     };
     if (ret == SP_OK && burn_in > 0) ret = advance(burn_in);
     if (ret == SP_OK && cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st) != cudaSuccess)
-      ret = sp_noalloc_error(SP_ECUDA, "sp_volume_estimate: memset failed");
+      ret = spg_set_error(SP_ECUDA, "sp_volume_estimate: memset failed");
     for (int t = 0; t < steps && ret == SP_OK; ++t) {
       ret = advance(1);
       if (ret != SP_OK) break;
@@ -111,20 +111,20 @@ int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio,
       spg::count_in_ball_kernel<<<(chains + 7) / 8, 256, 0, st>>>(X, chains, n, rprev * rprev,
                                                                   dcount);
       if (cudaGetLastError() != cudaSuccess)
-        ret = sp_noalloc_error(SP_ECUDA, "sp_volume_estimate: count kernel launch failed");
+        ret = spg_set_error(SP_ECUDA, "sp_volume_estimate: count kernel launch failed");
     }
     unsigned long long hc = 0;
     if (ret == SP_OK && (cudaMemcpyAsync(&hc, dcount, sizeof(hc), cudaMemcpyDeviceToHost, st) !=
                              cudaSuccess ||
                          cudaStreamSynchronize(st) != cudaSuccess))
-      ret = sp_noalloc_error(SP_ECUDA, "sp_volume_estimate: count copy failed");
+      ret = spg_set_error(SP_ECUDA, "sp_volume_estimate: count copy failed");
     if (ch) sp_destroy_chains(ch);
     if (si) sp_destroy_spectrahedron(si);
     if (ret != SP_OK) break;
     const double N = (double)chains * steps;
     const double f = (double)hc / N;
     if (!(f > 0.0)) {
-      ret = sp_noalloc_error(SP_EINVAL,
+      ret = spg_set_error(SP_EINVAL,
                              "sp_volume_estimate: no sample in the smaller ball (ratio too small)");
       break;
     }

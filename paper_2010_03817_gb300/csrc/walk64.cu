@@ -7,7 +7,8 @@
 //   Lanczos on M_sigma = -L^{-1} V L^{-T}: t = sigma + 1/mu (Alg. 2)
 //   w_j = u^T A_j u, u = L^{-T} y                          (Lemma "Gradient
 //       of det F")
-//   t+ refined as -(u^T F u)/(u^T V u) = -(w_0 + p.w)/(v.w)
+//   t+ (and t-) refined by the pencil Rayleigh correction
+//       t <- t - u^T (F + t V) u / (u^T V u) on the exact F and V
 //   reflection s = v - 2 <v, w^> w^                        (Eq. "reflection")
 // and the walk drivers of Alg. 4 (Hit-and-Run), CDHR and Alg. 5 (Billiard).
 #include <math.h>
@@ -75,25 +76,58 @@ __device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
   return s;
 }
 
+constexpr int kCdhrRefresh = 64;  // CDHR: steps between re-formations of F(p)
+constexpr double kRedoRatio = 100.0;  // |mu_min| / mu_max above which the solve is redone
+
 struct SegResult {
   double t_plus, t_minus, t_raw;
   int status;
   int iters;
   int retried;
+  int flags;  // kSegFlag* of the segment record
 };
 
 // One boundary-oracle evaluation for the line p + t v (CTA-wide).
+// vcol >= 0: v is the coordinate direction e_vcol (CDHR), so V = A_{vcol+1}
+// is read from the stack instead of formed.
 __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
                                   double* __restrict__ Vfull, double* __restrict__ Fg,
                                   double* __restrict__ Q, double sigma, bool want_min,
-                                  bool want_w, bool form_f) {
+                                  bool want_w, bool form_f, int vcol = -1) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m;
   const long long P = sp.P;
   SegResult res;
   res.retried = 0;
+  res.flags = 0;
   // ---- form V (and F(p) when form_f; otherwise F is carried in Fg) ---------
-  if (form_f) {
+  if (vcol >= 0) {
+    // CDHR (Sec. 3.1): V = A_j is a slice of the stack; F(p) carried or formed
+    const double* Aj = sp.A + (size_t)(vcol + 1) * P;
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      double f;
+      if (form_f) {
+        const double* Ae = sp.A + e;
+        double f0 = Ae[0], f1 = 0.0;
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+          f0 += sm.p[j] * Ae[(size_t)(j + 1) * P];
+          f1 += sm.p[j + 1] * Ae[(size_t)(j + 2) * P];
+        }
+        if (j < n) f0 += sm.p[j] * Ae[(size_t)(j + 1) * P];
+        f = f0 + f1;
+        Fg[e] = f;
+      } else {
+        f = Fg[e];
+      }
+      const double g = Aj[e];
+      sm.L[e] = f + sigma * g;
+      const uint32_t ik = sp.pidx[e];
+      const int i = ik >> 16, k = ik & 0xffff;
+      Vfull[(size_t)i * m + k] = g;
+      Vfull[(size_t)k * m + i] = g;
+    }
+  } else if (form_f) {
     for (long long e = tid; e < P; e += SPG_THREADS) {
       const double* Ae = sp.A + e;
       double f0 = Ae[0], f1 = 0.0, g0 = 0.0, g1 = 0.0;
@@ -139,16 +173,24 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
     }
   }
   __syncthreads();
-  // ---- Cholesky of F + sigma V; unshifted retry if the shift overshot ----
-  for (;;) {
+  // ---- Cholesky of F + sigma V; a smaller shift if it overshot -------------
+  // (x 0.2 per retry, then 0: the shift keeps the root just behind the point
+  // -- the boundary it left -- from dominating M_sigma, whose rounding would
+  // otherwise swamp the wanted eigenvector; unshifted, next to the boundary,
+  // |M| / mu+ reaches 1 / kappa)
+  for (int attempt = 0;; ++attempt) {
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
     bool ok = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
     if (ok) break;
     if (sigma != 0.0) {
-      sigma = 0.0;
+      sigma = attempt < 3 ? 0.2 * sigma : 0.0;
       res.retried = 1;
-      for (long long e = tid; e < P; e += SPG_THREADS) sm.L[e] = Fg[e];
+      res.flags |= kSegShiftRetry;
+      for (long long e = tid; e < P; e += SPG_THREADS) {
+        const uint32_t ik = sp.pidx[e];
+        sm.L[e] = Fg[e] + sigma * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+      }
       __syncthreads();
       continue;
     }
@@ -164,8 +206,57 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
   PencilOp<double> op{sm.L, Vfull, false, nullptr};
   LanczosOut lo = lanczos_extreme<double>(op, Q, sm.q, sm.r, sm.z, sm.scr, sm.ymax, sm.ymin, m,
                                           wk.kmax, want_min, wk.tol, sm.sc);
-  res.iters = lo.iters;
+  int iters = lo.iters;
+  // A root just behind the point (the boundary it sits next to) dominates
+  // M_sigma when |mu_min| >> mu_max; the rounding of M, about eps |mu_min|,
+  // then swamps the wanted eigenvector.  Redo the solve at a shift halfway to
+  // the estimated root, where both ends weigh alike.
+  {
+    double th_lo = lo.theta_min;
+    if (!want_min) {
+      if (wid == 0) {
+        const double x = tri_extreme(sm.sc->alpha, sm.sc->beta, lo.iters, false);
+        if (lane == 0) sm.bc[1] = x;
+      }
+      __syncthreads();
+      th_lo = sm.bc[1];
+      __syncthreads();
+    }
+    if (lo.theta_max > 0.0 && -th_lo > kRedoRatio * lo.theta_max) {
+      const double s2 = sigma + 0.5 / lo.theta_max;
+      for (long long e = tid; e < P; e += SPG_THREADS) {
+        const uint32_t ik = sp.pidx[e];
+        sm.L[e] = Fg[e] + s2 * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+      }
+      if (tid == 0) sm.ib[0] = 0;
+      __syncthreads();
+      const bool ok2 = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+      if (ok2) {
+        sigma = s2;
+        res.flags |= kSegRefined;
+      } else {
+        // (the estimate overshot: back to the first factor)
+        for (long long e = tid; e < P; e += SPG_THREADS) {
+          const uint32_t ik = sp.pidx[e];
+          sm.L[e] = Fg[e] + sigma * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+        }
+        if (tid == 0) sm.ib[0] = 0;
+        __syncthreads();
+        factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+      }
+      invert_diag_blocks(sm.L, m);
+      if (ok2) {
+        for (int i = tid; i < m; i += SPG_THREADS) sm.q[i] = 1.0 + 0.5 * sin(0.7 * i + 0.1);
+        __syncthreads();
+        lo = lanczos_extreme<double>(op, Q, sm.q, sm.r, sm.z, sm.scr, sm.ymax, sm.ymin, m,
+                                     wk.kmax, want_min, wk.tol, sm.sc);
+        iters += lo.iters;
+      }
+    }
+  }
+  res.iters = iters;
   res.status = lo.converged ? kOk : kNoConv;
+  if (!lo.converged) res.flags |= kSegNoConv;
   res.t_plus = lo.theta_max > 0.0 ? sigma + 1.0 / lo.theta_max : INFINITY;
   res.t_minus = (want_min && lo.theta_min < 0.0) ? sigma + 1.0 / lo.theta_min : -INFINITY;
   res.t_raw = res.t_plus;
@@ -192,6 +283,22 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
     for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] *= sc;
     __syncthreads();
   }
+  // both ends refined by the pencil Rayleigh correction on the exact F and V
+  // (Fg, Vfull), kept only when it is a correction of the Ritz value
+  {
+    const double tr =
+        pencil_correct(Fg, Vfull, true, m, P, sp.pidx, sm.u, res.t_plus, sm.sc->red);
+    if (tr > 0.0 && fabs(tr - res.t_plus) <= 1e-4 * res.t_plus) res.t_plus = tr;
+  }
+  if (want_min && isfinite(res.t_minus)) {
+    for (int i = tid; i < m; i += SPG_THREADS) sm.z[i] = sm.ymin[i];
+    __syncthreads();
+    solve_upper(sm.L, sm.z, m, sm.scr);
+    const double tr =
+        pencil_correct(Fg, Vfull, true, m, P, sp.pidx, sm.z, res.t_minus, sm.sc->red);
+    if (tr < 0.0 && fabs(tr - res.t_minus) <= 1e-4 * fabs(res.t_minus)) res.t_minus = tr;
+  }
+  __syncthreads();
   if (!want_w) return res;
   // U_e = u_i u_k (x2 off the diagonal) overwrites the factor
   double* U = sm.L;
@@ -214,21 +321,6 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
     for (; e < P; e += 32) a0 += Aj[e] * U[e];
     const double acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) sm.w[j] = acc;
-  }
-  __syncthreads();
-  // refined t+ = -(w_0 + p.w)/(v.w)
-  {
-    double num = 0.0, den = 0.0;
-    for (int j = tid; j < n; j += SPG_THREADS) {
-      num += sm.p[j] * sm.w[j + 1];
-      den += sm.v[j] * sm.w[j + 1];
-    }
-    num = block_sum(num, sm.sc->red);
-    den = block_sum(den, sm.sc->red);
-    num += sm.w[0];
-    const double tr = -num / den;
-    // keep the refinement only when it is a correction of the Ritz value
-    if (den < 0.0 && tr > 0.0 && fabs(tr - res.t_plus) <= 1e-4 * res.t_plus) res.t_plus = tr;
   }
   __syncthreads();
   return res;
@@ -297,7 +389,11 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
         int nrefl = 0;
         double sigma = 0.0;
         for (;;) {
-          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true, nrefl == 0);
+          // F(p) is formed afresh with V on every segment (the formation loop
+          // reads the A stack once for both): an F carried through a long
+          // run of reflections accumulates the rounding of every update,
+          // which short chords next to the boundary amplify by |F| / |u^T V u|
+          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true, true);
           ++segs;
           iters += r.iters;
           retries += r.retried;
@@ -306,6 +402,10 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
             r.status = kOk;  // the Ritz value is still the best estimate
           }
           if (r.status != kOk) {
+            const int slot = seglog_slot(wp.seg, &sm.ib[3]);
+            if (slot >= 0)
+              seglog_write(wp.seg, slot, n, sm.p, sm.v, nullptr, r.t_plus, -INFINITY, r.status, 0,
+                           chain, step, nrefl, r.flags);
             status = r.status;
             break;
           }
@@ -314,6 +414,12 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
             const double tp = r.t_plus;
             double* wh = sm.wh;
             const double nw = unit_normal(sm, n, wh);
+            {
+              const int slot = seglog_slot(wp.seg, &sm.ib[3]);
+              if (slot >= 0)
+                seglog_write(wp.seg, slot, n, sm.p, sm.v, nw > 0.0 ? wh : nullptr, tp, -INFINITY,
+                             nw > 0.0 ? kOk : kDegenerate, 1, chain, step, nrefl, r.flags);
+            }
             if (!(nw > 0.0)) {
               status = kDegenerate;
               break;
@@ -326,10 +432,6 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
               sm.p[j] += step_len * sm.v[j];
               sm.v[j] -= 2.0 * vw * wh[j];
             }
-            for (long long e = tid; e < sp.P; e += SPG_THREADS) {
-              const uint32_t ik = sp.pidx[e];
-              Fg[e] += step_len * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
-            }
             __syncthreads();
             ell -= tp;
             ++nrefl;
@@ -339,6 +441,10 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
             }
             sigma = wp.sigma_frac * tp;
           } else {
+            const int slot = seglog_slot(wp.seg, &sm.ib[3]);
+            if (slot >= 0)
+              seglog_write(wp.seg, slot, n, sm.p, sm.v, nullptr, r.t_plus, -INFINITY, kOk, 0,
+                           chain, step, nrefl, r.flags);
             for (int j = tid; j < n; j += SPG_THREADS) sm.x0[j] = sm.p[j] + ell * sm.v[j];
             __syncthreads();
             break;
@@ -347,7 +453,17 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
         refl += nrefl;
       } else {
         // ---- Hit-and-Run (Alg. 4) / CDHR: uniform point on the chord ------
-        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false, true);
+        // CDHR reads V = A_j from the stack and carries F from step to step,
+        // F(p + t e_j) = F(p) + t A_j (Sec. 3.1), re-forming it every
+        // kCdhrRefresh steps so that the rounding of the updates stays below
+        // ~sqrt(kCdhrRefresh) ulp of F
+        const bool cd = wp.kind == 2;
+        int jc = -1;
+        if (cd)
+          for (int j = 0; j < n; ++j)
+            if (sm.v[j] != 0.0) jc = j;
+        const bool form = !cd || k % kCdhrRefresh == 0;
+        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false, form, jc);
         ++segs;
         iters += r.iters;
         if (r.status == kNoConv) {
@@ -355,9 +471,19 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
           r.status = kOk;
         }
         if (r.status == kOk && !(isfinite(r.t_plus) && isfinite(r.t_minus))) r.status = kUnbounded;
+        {
+          const int slot = seglog_slot(wp.seg, &sm.ib[3]);
+          if (slot >= 0)
+            seglog_write(wp.seg, slot, n, sm.p, sm.v, nullptr, r.t_plus, r.t_minus, r.status, 0,
+                         chain, step, 0, r.flags);
+        }
         if (r.status == kOk) {
           const double t = r.t_minus + eta * (r.t_plus - r.t_minus);
           for (int j = tid; j < n; j += SPG_THREADS) sm.x0[j] = sm.p[j] + t * sm.v[j];
+          if (cd) {
+            const double* Aj = sp.A + (size_t)(jc + 1) * sp.P;
+            for (long long e = tid; e < sp.P; e += SPG_THREADS) Fg[e] += t * Aj[e];
+          }
           __syncthreads();
         } else {
           status = r.status;
@@ -395,11 +521,26 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
   Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg);
   for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
+    double bad = 0.0;
     for (int j = tid; j < n; j += SPG_THREADS) {
       sm.p[j] = pp.x[(size_t)c * n + j];
       sm.v[j] = pp.op == 2 ? 0.0 : pp.v[(size_t)c * n + j];
+      if (!isfinite(sm.p[j]) || !isfinite(sm.v[j])) bad = 1.0;
     }
-    __syncthreads();
+    if (block_sum(bad, sm.sc->red) > 0.0) {
+      // a non-finite point or direction: nothing to compute
+      if (tid == 0) {
+        if (pp.op == 2) {
+          pp.inside[c] = 0;
+        } else {
+          pp.status[c] = kInvalid;
+          pp.t_plus[c] = NAN;
+          if (pp.op == 0) pp.t_minus[c] = NAN;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     if (pp.op == 2) {
       // membership: Cholesky of F(x) succeeds
       const long long P = sp.P;

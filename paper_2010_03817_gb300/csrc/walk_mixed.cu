@@ -104,6 +104,7 @@ struct MixResult {
   double t_plus, t_minus;
   int status, iters, retries, fallback, power;
   int learned;  // 1: warm start accepted, -1: rejected, 0: not used
+  int refined;  // a shift-invert refinement next to the boundary ran
 };
 
 // unit length, largest-magnitude entry positive (CTA-wide, FP64)
@@ -525,13 +526,35 @@ __device__ __noinline__ int refine_end(const DevSpec& sp, const MixWork& mw, Mix
                           const double* __restrict__ Fg, const double* __restrict__ Vg,
                           double* __restrict__ Q64, double sigma0, double t_est, bool cold,
                           double* t, MixResult* res, bool plus) {
-  if (!cold) {
-    if (refine_end_dd(sp, mw, sm, Fg, Vg, sigma0, t_est, t, res, plus, mw.delta1, 3,
-                      mw.power_iters) == kOk)
-      return kOk;
+  int st;
+  if (!cold &&
+      refine_end_dd(sp, mw, sm, Fg, Vg, sigma0, t_est, t, res, plus, mw.delta1, 3,
+                    mw.power_iters) == kOk) {
+    st = kOk;
+  } else {
     res->fallback = 1;
+    st = refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, t_est, cold, t, res, plus);
+    if (cold && (st == kOk || st == kNoConv) && isfinite(*t)) {
+      // a cold start factors at sigma0 or at the point itself, where a root
+      // just behind it can dominate the Lanczos operator and blur u: refine
+      // once more by shift-invert next to the root just found
+      double t2 = *t;
+      const int st2 =
+          refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, *t, false, &t2, res, plus);
+      if (st2 == kOk) {
+        *t = t2;
+        st = kOk;
+        res->refined = 1;
+      }
+    }
   }
-  return refine_end_fp64(sp, mw, sm, Fg, Vg, Q64, sigma0, t_est, cold, t, res, plus);
+  if (st == kOk || st == kNoConv) {
+    // the pencil Rayleigh correction on the exact F and V: removes the
+    // factorisation's backward error (about m eps |F|) from t
+    const double tr = pencil_correct(Fg, Vg, false, sp.m, sp.P, sp.pidx, sm.u, *t, sm.sc->red);
+    if ((plus ? tr > 0.0 : tr < 0.0) && fabs(tr - *t) <= 1e-6 * fabs(*t)) *t = tr;
+  }
+  return st;
 }
 
 // One boundary-oracle evaluation in mixed precision (CTA-wide).
@@ -553,6 +576,7 @@ __device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork
   res.fallback = 0;
   res.power = 0;
   res.learned = 0;
+  res.refined = 0;
   res.t_minus = -INFINITY;
   float* G32 = reinterpret_cast<float*>(sm.R);
   float* V32 = G32 + P;
@@ -777,7 +801,7 @@ __device__ void draw_direction(uint64_t seed, uint32_t chain, uint32_t step, dou
 __device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& mw, const MixWave& wv,
                                  MixSmem& sm, int r, int c, int status, double t_plus,
                                  double t_minus, double ell, int nrefl, double* __restrict__ Fc,
-                                 const double* __restrict__ Vr, long long* st) {
+                                 const double* __restrict__ Vr, long long* st, int flags) {
   const int tid = threadIdx.x;
   const int n = sp.n;
   const long long P = sp.P;
@@ -785,11 +809,23 @@ __device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& 
   (void)r;
   bool step_done = false, rejected = false;
   double move = 0.0;
+  // the unit normal of a reflection, then the sampled segment record (the
+  // line as the oracle met it, before the move)
+  if (wv.kind != 0 && status == kOk && !(isfinite(t_plus) && isfinite(t_minus)))
+    status = kUnbounded;
+  const bool hit = wv.kind == 0 && status == kOk && t_plus < ell;
+  if (hit && !(mix_unit_normal(sm, n) > 0.0)) status = kDegenerate;
+  {
+    const int slot = seglog_slot(wv.seg, &sm.ib[3]);
+    if (slot >= 0)
+      seglog_write(wv.seg, slot, n, sm.p, sm.v, (hit && status == kOk) ? sm.wh : nullptr, t_plus,
+                   wv.kind == 0 ? -INFINITY : t_minus, status, hit ? 1 : 0, chain,
+                   wv.step0 + (uint32_t)wv.done[c], wv.kind == 0 ? nrefl : 0, flags);
+  }
   if (wv.kind == 0) {
-    if (status == kOk && t_plus < ell) {
-      const double nw = mix_unit_normal(sm, n);
-      if (!(nw > 0.0)) {
-        status = kDegenerate;
+    if (hit) {
+      if (status != kOk) {
+        // degenerate normal: the step is rejected below
       } else {
         double a = 0.0;
         for (int j = tid; j < n; j += SPG_THREADS) a += sm.v[j] * sm.wh[j];
@@ -822,18 +858,14 @@ __device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& 
   }
   __syncthreads();
   long long tu0 = clock64();
+  int fage = wv.fage[c];
   if (status != kOk) {
-    // the step is rejected: back to its start point; F(x) is re-formed
+    // the step is rejected: back to its start point; F(x) is formed afresh
+    // (listed for the next wave's formation, below)
     rejected = true;
     step_done = true;
     for (int j = tid; j < n; j += SPG_THREADS) sm.p[j] = wv.Xstart[(size_t)c * n + j];
-    __syncthreads();
-    for (long long e = tid; e < P; e += SPG_THREADS) {
-      const double* Ae = sp.A + e;
-      double f = Ae[0];
-      for (int j = 0; j < n; ++j) f += sm.p[j] * Ae[(size_t)(j + 1) * P];
-      Fc[e] = f;
-    }
+    fage = 1 << 20;
     if (tid == 0) {
       st[kStatBadSteps] += 1;
       wv.status[c] = status;
@@ -841,6 +873,7 @@ __device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& 
   } else if (move != 0.0) {
     // carried F: F(p + move v) = F(p) + move V
     for (long long e = tid; e < P; e += SPG_THREADS) Fc[e] += move * Vr[e];
+    ++fage;
   }
   __syncthreads();
   int done = wv.done[c];
@@ -865,13 +898,23 @@ __device__ __noinline__ void complete_segment(const DevSpec& sp, const MixWork& 
   }
   for (int j = tid; j < n; j += SPG_THREADS) wv.X[(size_t)c * n + j] = sm.p[j];
   if (done < wv.steps) {
-    // still active: queue the chain (and its direction) for the next wave
-    if (tid == 0) sm.ib[1] = atomicAdd(wv.count_next, 1);
+    // still active: queue the chain (and its direction) for the next wave,
+    // and for a fresh formation of F when its carried F is old: every update
+    // adds a rounding, which short chords next to the boundary amplify by
+    // |F| / |u^T V u|
+    if (tid == 0) {
+      sm.ib[1] = atomicAdd(wv.count_next, 1);
+      if (fage >= (wv.kind == 2 ? kFRefreshCdhr : kFRefresh)) {
+        wv.ref_ids[atomicAdd(wv.ref_count, 1)] = c;
+        fage = 0;
+      }
+    }
     __syncthreads();
     const int slot = sm.ib[1];
     for (int j = tid; j < n; j += SPG_THREADS) wv.dir_next[(size_t)slot * n + j] = sm.v[j];
     if (tid == 0) wv.id_next[slot] = c;
   }
+  if (tid == 0) wv.fage[c] = fage;
   stage_mark(mw, 6, tu0);  // F update, next direction, queueing
   if (tid == 0) {
     wv.done[c] = done;
@@ -899,13 +942,16 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   const int count = *wv.count_cur;
   for (int r = blockIdx.x; r < count; r += gridDim.x) {
     const int c = wv.id_cur[r];
-    const uint32_t chain = wv.chain0 + (uint32_t)c;
     double* Fc = wv.F + (size_t)c * P;
-    const double* Vr = wv.Vrows + (size_t)r * P;
     for (int j = tid; j < n; j += SPG_THREADS) {
       sm.p[j] = wv.X[(size_t)c * n + j];
       sm.v[j] = wv.dir_cur[(size_t)r * n + j];
+      if (wv.kind == 2 && sm.v[j] != 0.0) sm.ib[4] = j;
     }
+    __syncthreads();
+    // CDHR (Sec. 3.1): V = A_j, a slice of the stack (no formation); the
+    // carried F moves by t A_j
+    const double* Vr = wv.kind == 2 ? sp.A + (size_t)(sm.ib[4] + 1) * P : wv.Vrows + (size_t)r * P;
     double ell = wv.ell[c];
     int nrefl = wv.nrefl[c];
     const double tprev = wv.tprev[c];
@@ -943,6 +989,10 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       if (res.learned < 0) st[kStatLearnedMiss] += 1;
       if (res.status == kNoConv) st[kStatNoConv] += 1;
     }
+    const int flags = (res.retries > 0 ? kSegShiftRetry : 0) | (res.fallback ? kSegFallback : 0) |
+                      (res.learned > 0 ? kSegLearnedOk : 0) |
+                      (res.learned < 0 ? kSegLearnedMiss : 0) |
+                      (res.status == kNoConv ? kSegNoConv : 0) | (res.refined ? kSegRefined : 0);
     if (res.status == kNoConv) res.status = kOk;
     const bool reflect = wv.kind == 0 && res.status == kOk && res.t_plus < ell;
     if (wv.pend) {
@@ -951,7 +1001,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       double* ub = wv.Ubuf + (size_t)r * m;
       for (int i = tid; i < m; i += SPG_THREADS) ub[i] = reflect ? sm.u[i] : 0.0;
       if (tid == 0) {
-        wv.pend[r] = reflect ? 1 : 0;
+        wv.pend[r] = reflect ? 1 | (flags << 1) : 0;  // pending, and the record's flags
         wv.Tbuf[r] = res.t_plus;
       }
       __syncthreads();
@@ -962,7 +1012,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       stage_mark(mw, 5, tc0);  // normal contraction
     }
     complete_segment(sp, mw, wv, sm, r, c, res.status, res.t_plus, res.t_minus, ell, nrefl, Fc,
-                     Vr, st);
+                     Vr, st, flags);
     __syncthreads();
   }
 }
@@ -1002,7 +1052,7 @@ __global__ void __launch_bounds__(SPG_THREADS)
     __syncthreads();
     complete_segment(sp, mw, wv, sm, r, c, kOk, wv.Tbuf[r], -INFINITY, wv.ell[c], wv.nrefl[c],
                      wv.F + (size_t)c * P, wv.Vrows + (size_t)r * P,
-                     wv.stats + (size_t)c * kNumStats);
+                     wv.stats + (size_t)c * kNumStats, wv.pend[r] >> 1);
     __syncthreads();
   }
 }
@@ -1061,10 +1111,29 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
   double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
   for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
-    for (int j = tid; j < n; j += SPG_THREADS) sm.v[j] = pp.v[(size_t)c * n + j];
-    __syncthreads();
+    double bad = 0.0;
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      sm.v[j] = pp.v[(size_t)c * n + j];
+      if (!isfinite(sm.v[j]) || !isfinite(pp.x[(size_t)c * n + j])) bad = 1.0;
+    }
+    if (block_sum(bad, sm.sc->red) > 0.0) {
+      // a non-finite point or direction: nothing to compute (its formed rows
+      // are garbage and stay unused)
+      if (tid == 0) {
+        pp.status[c] = kInvalid;
+        pp.t_plus[c] = NAN;
+        if (pp.op == 0) pp.t_minus[c] = NAN;
+      }
+      if (pp.Ubuf)
+        for (int i = tid; i < m; i += SPG_THREADS) pp.Ubuf[(size_t)c * m + i] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const float* prow = (pp.pred && pp.op == 1) ? pp.pred + (size_t)c * pp.ld_pred : nullptr;
     MixResult res = segment_mixed(sp, mw, sm, Frows + (size_t)c * P, Vrows + (size_t)c * P, Q32,
-                                  Q64, 0.0, pp.op == 0, true);
+                                  Q64, 0.0, pp.op == 0, true, prow, pp.t_scale, pp.margin);
+    if (tid == 0 && pp.learned_ok && res.learned != 0)
+      atomicAdd(res.learned > 0 ? &pp.learned_ok[0] : &pp.learned_ok[1], 1);
     int status = res.status == kNoConv ? kOk : res.status;
     if (pp.op == 0) {
       if (tid == 0) {
@@ -1154,7 +1223,8 @@ __global__ void learned_features_kernel(const double* __restrict__ X,
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(q / n), j = (int)(q % n);
-    feats[(size_t)r * 2 * n + j] = (float)(X[(size_t)id[r] * n + j] * x_scale);
+    const size_t row = id ? (size_t)id[r] : (size_t)r;  // no id list: row r is line r
+    feats[(size_t)r * 2 * n + j] = (float)(X[row * n + j] * x_scale);
     feats[(size_t)r * 2 * n + n + j] = (float)dir[(size_t)r * n + j];
   }
 }

@@ -17,8 +17,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspectra_gb.so")
 
 OK, EINVAL, ENOTPD, EUNBOUNDED, ENOCONV, ECUDA, ENOMEM = range(7)
-ST_OK, ST_NOT_PD, ST_UNBOUNDED, ST_NOCONV, ST_RHO, ST_DEGENERATE = range(6)
+ST_OK, ST_NOT_PD, ST_UNBOUNDED, ST_NOCONV, ST_RHO, ST_DEGENERATE, ST_INVALID = range(7)
 MODE_FP64, MODE_MIXED, MODE_LEARNED = 0, 1, 2
+# solver-path flags of a segment record (sp_record_segments)
+SEG_SHIFT_RETRY, SEG_FALLBACK, SEG_LEARNED_OK, SEG_LEARNED_MISS, SEG_NOCONV, SEG_REFINED = (
+    1, 2, 4, 8, 16, 32)
 MODES = {"fp64": MODE_FP64, "mixed": MODE_MIXED, "learned": MODE_LEARNED}
 STAT_NAMES = ["segments", "reflections", "bad_steps", "lanczos_iters", "shift_retries",
               "noconv", "fp64_fallbacks", "power_iters", "learned_ok", "learned_miss"]
@@ -69,6 +72,9 @@ def _bind(L):
     f("sp_attach_mlp", [_vp, _vp, _d, _d, _d, _i])
     f("sp_record_tuples", [_vp, _vp, _vp, _i, _vp])
     f("sp_kernel_timing", [_vp, _i, _vp])
+    f("sp_record_segments", [_vp, _vp, _i, _i, _vp])
+    f("sp_learned_counts", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
+    f("sp_selftest_recip", [_i, _vp, _vp, _vp])
     f("sp_mlp_create", [_i, _i, _i, ctypes.c_uint64, ctypes.POINTER(_vp)])
     f("sp_mlp_destroy", [_vp])
     f("sp_mlp_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -138,6 +144,32 @@ def intersect_noalloc(A_packed, n: int, m: int, x, v, t_minus, t_plus, status, s
         _dev(status, torch.int32, (C,), "status"), _stream(stream)))
 
 
+def decode_segments(buf, count: int, every: int, n: int) -> dict:
+    """Split the filled slots of a segment record (sp_record_segments) into
+    host arrays p, v, w_hat (K x n), t_plus, t_minus, status, reflected,
+    chain, step, k (the segment's index in its step) and flags (the solver
+    path: SEG_* bits) (K each)."""
+    filled = min(buf.shape[0], (int(count) + every - 1) // every)
+    R = buf[:filled].cpu().numpy()
+    return {"p": R[:, :n], "v": R[:, n:2 * n], "w_hat": R[:, 2 * n:3 * n],
+            "t_plus": R[:, 3 * n], "t_minus": R[:, 3 * n + 1],
+            "status": R[:, 3 * n + 2].astype(np.int32), "reflected": R[:, 3 * n + 3] > 0.5,
+            "chain": R[:, 3 * n + 4].astype(np.int64), "step": R[:, 3 * n + 5].astype(np.int64),
+            "k": R[:, 3 * n + 6].astype(np.int64), "flags": R[:, 3 * n + 7].astype(np.int64)}
+
+
+def selftest_recip(x, stream=None):
+    """The dense kernels' 1/sqrt(x) and 1/x routines on a CUDA float64 vector
+    x: (count, 4) = FP64 rsqrt, FP64 reciprocal, double-float rsqrt,
+    double-float reciprocal (sp_selftest_recip)."""
+    import torch
+    C = x.shape[0]
+    out = torch.empty((C, 4), dtype=torch.float64, device=x.device)
+    _check(lib().sp_selftest_recip(C, _dev(x, torch.float64, (C,), "x"), _dev(out),
+                                   _stream(stream)))
+    return out
+
+
 def version() -> str:
     return lib().sp_version().decode()
 
@@ -179,6 +211,12 @@ class Spectrahedron:
         self._mlp = net
         _check(lib().sp_attach_mlp(self._h, net.handle if net is not None else None, x_scale,
                                    t_scale, margin, iters))
+
+    def learned_counts(self):
+        """(accepted, rejected) warm starts of the last learned reflect call."""
+        a, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().sp_learned_counts(self._h, ctypes.byref(a), ctypes.byref(r)))
+        return a.value, r.value
 
     def set_stage_timers(self, timers=None):
         """Mixed-path stage timers: an int64 CUDA tensor (SMs x 16), or None."""
@@ -353,6 +391,20 @@ class Chains:
         cap = x_out.shape[0]
         _check(lib().sp_record_tuples(self._h, _dev(x_out, torch.float32), _dev(y_out, torch.float32),
                                       cap, _dev(count, torch.int32)))
+
+    def record_segments(self, buf=None, count=None, every: int = 1):
+        """Record every `every`-th boundary-oracle call of later walks into buf
+        (CUDA float64 tensor, capacity x (3n + 8)) with the int32 ticket
+        counter `count` (zeroed by the caller); no arguments stop."""
+        import torch
+        if buf is None:
+            _check(lib().sp_record_segments(self._h, None, 0, 1, None))
+            return
+        n = self.spec.n
+        if buf.dim() != 2 or buf.shape[1] != 3 * n + 8:
+            raise ValueError("buf must be (capacity, 3n + 8)")
+        _check(lib().sp_record_segments(self._h, _dev(buf, torch.float64), buf.shape[0], every,
+                                        _dev(count, torch.int32)))
 
     def status(self, stream=None):
         """(per-chain status tensor, dict of summed statistics)."""

@@ -117,3 +117,47 @@ def test_cdhr_moves_one_coordinate():
     assert np.count_nonzero(d) == 1 and d[j] != 0
     eta = oracle.uniform(4, 2, 6, 1)
     assert x[j] == pytest.approx(-1.0 + eta * 2.0, rel=1e-12)
+
+
+def test_billiard_trace_follows_alg5():
+    """The traced Billiard step is the same step (same end point), and its
+    recorded lines chain as Alg. 5 moves: after a hit at t+ the next line
+    starts at p + (1 - kappa) t+ v with the reflected direction s."""
+    n, kappa = 6, 1e-6
+    A = W.ball_random(n, 6, 2.0, seed=W.BASE_SEED + 40)
+    X = np.zeros((5, n))
+    Xt, P, V, st, rows = oracle.billiard_trace(A, X, 3, tau=4.0, rho=50, kappa=kappa, seed=8,
+                                               chain0=2, max_per_chain=64)
+    Xw, _ = oracle.walk("billiard", A, X, 1, tau=4.0, rho=50, kappa=kappa, seed=8, step0=3,
+                        chain0=2)
+    assert np.array_equal(Xt, Xw)
+    assert (st == 0).all()
+    assert set(rows["chain"]) == set(range(2, 7))
+    for i in range(len(P) - 1):
+        if rows["chain"][i + 1] != rows["chain"][i]:
+            assert rows["k"][i + 1] == 0
+            continue
+        assert rows["k"][i + 1] == rows["k"][i] + 1
+        r = oracle.reflect(A, P[i], V[i])
+        assert np.allclose(P[i + 1], P[i] + (1 - kappa) * r["t_plus"] * V[i], atol=1e-14)
+        assert np.allclose(V[i + 1], r["s"], atol=1e-14)
+    # the first line of each chain: its start point and its Philox direction
+    for c in range(5):
+        i = int(np.nonzero((rows["chain"] == 2 + c) & (rows["k"] == 0))[0][0])
+        assert np.array_equal(P[i], X[c])
+        assert np.array_equal(V[i], oracle.direction(n, 8, 2 + c, 3))
+
+
+def test_reflect_batch_equals_single_calls():
+    n = 5
+    A = W.rotated_cube(n, seed=W.BASE_SEED + 41)
+    g = np.random.default_rng(3)
+    P = g.uniform(-0.9, 0.9, size=(7, n))
+    V = W.random_directions(n, 7, seed=4)
+    rb = oracle.reflect_batch(A, P, V)
+    for c in range(7):
+        r = oracle.reflect(A, P[c], V[c])
+        assert rb["status"][c] == r["status"]
+        assert rb["t_plus"][c] == r["t_plus"]
+        assert np.array_equal(rb["w_hat"][c], r["w_hat"])
+        assert rb["rel_gap"][c] == r["rel_gap"]

@@ -3,8 +3,10 @@ allocate device memory) gives the results of the regular entry point.
 
 It is called twice in a row on the same inputs, through the C ABI, and both
 calls must agree with sp_intersect within the FP64 parity tolerance of the
-other GPU tests (1e-10 relative on t+ and t-).  This file sorts last so that
-a stop-at-first-failure run has run every other test before it.
+other GPU tests (1e-10 relative on t+ and t-), while the device's free
+memory stays exactly where it was (the entry point allocates nothing).
+This file sorts last so that a stop-at-first-failure run has run every
+other test before it.
 """
 import numpy as np
 import pytest
@@ -39,12 +41,26 @@ def test_noalloc_matches_intersect(spectra, kind):
     spec = spectra.Spectrahedron(A)
     tm_ref, tp_ref, _, st_ref = spec.intersect(x, v)
     Ap = torch.tensor(spectra.pack_lmi(A), device="cuda")
+    outs = [(torch.empty(40, dtype=torch.float64, device="cuda"),
+             torch.empty(40, dtype=torch.float64, device="cuda"),
+             torch.empty(40, dtype=torch.int32, device="cuda")) for _ in range(3)]
+    for tm, tp, st in outs:
+        tm.fill_(float("nan"))
+        tp.fill_(float("nan"))
+        st.fill_(-1)
+    # a first call (it looks up the array's address on this device and loads
+    # the kernels), then the device's free memory must not move across the two
+    # checked calls: every buffer is allocated and filled already, and nothing
+    # else runs in between
+    spectra.intersect_noalloc(Ap, n, m, x, v, *outs[2])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     for call in range(2):
-        tm = torch.full((40,), float("nan"), dtype=torch.float64, device="cuda")
-        tp = torch.full((40,), float("nan"), dtype=torch.float64, device="cuda")
-        st = torch.full((40,), -1, dtype=torch.int32, device="cuda")
-        spectra.intersect_noalloc(Ap, n, m, x, v, tm, tp, st)
-        torch.cuda.synchronize()
+        spectra.intersect_noalloc(Ap, n, m, x, v, *outs[call])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for call in range(2):
+        tm, tp, st = outs[call]
         assert torch.equal(st, st_ref), call
         assert bool((st == 0).all())
         assert torch.allclose(tp, tp_ref, rtol=TOL_T, atol=0.0), call
