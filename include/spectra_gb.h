@@ -208,6 +208,59 @@ int sp_volume_estimate(sp_spec* s, double r_inner, double r_outer, double ratio,
                        double* info, void* stream);
 
 /*
+ * The Monte Carlo estimate of the expected value of f(x) = 1(c.x <= b1 or
+ * c.x >= b2) -- the indicator of S cap H for the union H of two half-spaces
+ * (Sec. 4.2) -- over the chains' current points, in `groups` consecutive
+ * groups of C / groups chains: frac_out[g] (host) = the fraction of group g's
+ * points in H.  c: host or device, n doubles.  SP_EINVAL unless groups
+ * divides C and b1 < b2.  Synchronises `stream`.
+ */
+int sp_halfspace_fraction(sp_chains* ch, const double* c, double b1, double b2, int groups,
+                          double* frac_out, void* stream);
+
+/*
+ * A batch of spectrahedra of uneven sizes (n, m) walked together: the
+ * Billiard walk (Sec. 3.2, Alg. 5) of every chain of every body in ONE
+ * persistent launch on the FP64 path.  Work items are (body, chain) pairs
+ * handed out by a device-side queue in decreasing order of the estimated
+ * cost of a segment (formation, Cholesky, Lanczos, normal), so that the
+ * longest items start first; a block carves its shared memory for each
+ * item's body (factor in shared memory when it fits, else in global
+ * memory) and runs all its steps with the body's Cholesky panel width.
+ *   sp_create_batch : bodies handles (not owned; they must outlive the
+ *                     batch), chains[i] chains each, all starting at their
+ *                     body's origin (checked interior: SP_ENOTPD); body i's
+ *                     chain c draws from Philox chain chain0_i + c with
+ *                     chain0_i = chains[0] + ... + chains[i-1], key `seed`.
+ *   sp_batch_billiard: `steps` steps of every chain; tau (host, one per
+ *                     body), rho, kappa as in sp_step_billiard.
+ *   sp_batch_dims   : n, m, chains and chain0 of body i (host outputs, may be NULL).
+ *   sp_batch_state  : x_out (host or device, chains[i] x n) <- body i's points.
+ *   sp_batch_stats  : stats (host, bodies x SP_NUM_STATS) summed per body.
+ *   sp_batch_panels : read (panel_out) and / or set (panel_in) the Cholesky
+ *                     panel widths (host, one per body: 4, 8 or 16; default 8).
+ *   sp_batch_tune   : the autotuner: for every body, the panel width whose
+ *                     calibration (REFLECTION of two lines per SM from the
+ *                     origin, one untimed and one timed launch per width) is
+ *                     fastest; results are cached per (device name, n, m) in
+ *                     the text file cache_path (read if present, rewritten
+ *                     with new entries; NULL: no cache).  times_out (host,
+ *                     bodies x 3, may be NULL): the calibration ms of widths
+ *                     4, 8, 16 (from the cache when found there).
+ */
+typedef struct sp_batch sp_batch;
+int sp_create_batch(int bodies, sp_spec* const* specs, const int* chains, uint64_t seed,
+                    sp_batch** out, void* stream);
+int sp_destroy_batch(sp_batch* b);
+int sp_batch_billiard(sp_batch* b, int steps, const double* tau, int rho, double kappa,
+                      void* stream);
+int sp_batch_dims(const sp_batch* b, int body, int* n, int* m, int* chains, int* chain0);
+int sp_batch_state(sp_batch* b, int body, double* x_out, uint32_t* step_out, void* stream);
+int sp_batch_stats(sp_batch* b, long long* stats, void* stream);
+int sp_batch_panels(sp_batch* b, int* panel_out, const int* panel_in);
+int sp_batch_tune(sp_batch* b, const char* cache_path, double* times_out, void* stream);
+
+/*
  * Chain state.
  *   sp_get_state: x_out (host or device, C x n) <- current points; *step_out <-
  *                 the next step number.  Synchronises `stream` when x_out is host.
@@ -311,8 +364,12 @@ int sp_attach_mlp(sp_spec* s, sp_mlp* q, double x_scale, double t_scale, double 
  * FP64 divide and square root): for each x[c] (device, count float64)
  * out[4c .. 4c+3] (device) = 1/sqrt(x) and 1/x from an FP32 seed refined by
  * two Newton steps in FP64, then the same two in double-float arithmetic
- * (rounded to FP64).  Valid for x in [1e-37, 3e37], the range the Cholesky
- * accepts as pivots (outside it the factorisation reports failure).
+ * (rounded to FP64).  The FP64 versions hold for x in [1e-37, 3e37], the
+ * range the Cholesky accepts as pivots (outside it the factorisation reports
+ * failure); the double-float ones for x in [2^-62, 2^100] (below, the
+ * conversion of an FP64 x to a pair keeps only its FP32 part; above, the low
+ * parts of the intermediate products leave the FP32 normal range), far
+ * beyond the O(1) to O(10^4) pivots of the workloads here.
  */
 int sp_selftest_recip(int count, const double* x, double* out, void* stream);
 

@@ -318,7 +318,13 @@ int spec_copy_stack(const sp_spec* s, double* packed_host) {
     return cuda_fail(cudaGetLastError(), "LMI stack copy");
   return SP_OK;
 }
+DevSpec spec_dev(const sp_spec* s) { return s->dev(); }
 const double* chain_points(const sp_chains* ch) { return ch->X; }
+const double* chain_points(const sp_chains* ch, int* C, int* n) {
+  *C = ch->C;
+  *n = ch->spec->n;
+  return ch->X;
+}
 }  // namespace spg
 
 extern "C" {

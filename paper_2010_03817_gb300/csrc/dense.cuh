@@ -41,7 +41,8 @@ __device__ __forceinline__ void mac_acc(T& acc, T a, T b) {
 }
 
 // In-place Cholesky G = L L^T of the packed lower triangle G (m x m),
-// right-looking in panels of kPanel = 8 columns, three barriers per panel:
+// right-looking in panels of kPanel columns (8 unless the caller picks 4 or
+// 16), three barriers per panel:
 //   1. warp 0 factors the 8 x 8 diagonal block in registers (lane r holds
 //      row r of the block; column c is broadcast by shuffles);
 //   2. every row below solves against it (one thread per row, forward
@@ -49,14 +50,15 @@ __device__ __forceinline__ void mac_acc(T& acc, T a, T b) {
 //      leaves its 8 entries in the transposed panel copy pan[c][i];
 //   3. the trailing lower triangle receives the rank-8 update in 4 x 4
 //      register tiles (8 + 8 panel loads per 128 FMAs).
-// pan: scratch of cholesky_scratch(m) elements.  Returns true on success
+// pan: scratch of cholesky_scratch(m, kPanel) elements.  Returns true on success
 // (CTA-uniform); on failure *flag = 1 + the first column whose pivot was not
 // positive (or outside the range where the FP32-seeded reciprocal square root
 // holds).
-constexpr int kPanel = 8;
+constexpr int kPanel = 8;      // the default panel width
+constexpr int kMaxPanel = 16;  // the widest panel a kernel may choose
 __host__ __device__ inline int chol_ld(int m) { return (m + 6) & ~3; }
-__host__ __device__ inline size_t cholesky_scratch(int m) {
-  return (size_t)kPanel * chol_ld(m) + 4;
+__host__ __device__ inline size_t cholesky_scratch(int m, int pw = kPanel) {
+  return (size_t)pw * chol_ld(m) + 4;
 }
 
 // four consecutive elements from 16-byte aligned shared memory (vector loads)
@@ -75,7 +77,7 @@ __device__ __forceinline__ void load4(const T* p, T (&v)[4]) {
   }
 }
 
-template <typename T>
+template <typename T, int kPanel = spg::kPanel>
 __device__ bool factor_cholesky(T* G, int m, T* pan_raw, int* flag) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // 16-byte aligned panel base; row stride ld (a multiple of 4, >= m + 3)
@@ -409,6 +411,79 @@ __device__ void mul_upper(const T* L, const T* x, T* y, int m, T* part) {
     y[k] = s;
   }
   __syncthreads();
+}
+
+// s + e = a + b exactly (TwoSum, FP64)
+__device__ __forceinline__ void two_sum64(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// CTA-wide compensated sum of the pairs (s, c) (value s + c on every
+// thread): TwoSum at every level of the tree.  red: 2 SPG_WARPS doubles.
+__device__ __forceinline__ double block_sum_dd(double s, double c, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double so = __shfl_xor_sync(0xffffffffu, s, o);
+    const double co = __shfl_xor_sync(0xffffffffu, c, o);
+    double e;
+    two_sum64(s, so, s, e);
+    c += co + e;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[2 * wid] = s;
+    red[2 * wid + 1] = c;
+  }
+  __syncthreads();
+  s = 0.0;
+  c = 0.0;
+#pragma unroll
+  for (int w = 0; w < SPG_WARPS; ++w) {
+    double e;
+    two_sum64(s, red[2 * w], s, e);
+    c += red[2 * w + 1] + e;
+  }
+  return s + c;
+}
+
+// The pencil Rayleigh correction of the FP64 path, with F(p) = A_0 + Y kept
+// in two parts (Y = sum_{j>=1} p_j A_j): the large and exact A_0 part of
+//   u^T (F + t0 V) u = u^T A_0 u + u^T (Y + t0 V) u
+// is summed with error-free products and sums (Ogita, Rump, Oishi 2005,
+// Dot2), so that neither the rounding of A_0 + Y nor that of the sum enters
+// t; the small part in plain FP64.  Arguments as pencil_correct; A0 packed
+// (global); red: 2 SPG_WARPS doubles.
+__device__ inline double pencil_correct_split(const double* __restrict__ A0,
+                                              const double* __restrict__ Y,
+                                              const double* __restrict__ V, bool vfull, int m,
+                                              long long P, const uint32_t* __restrict__ pidx,
+                                              const double* u, double t0, double* red) {
+  double s = 0.0, c = 0.0, a = 0.0, b = 0.0;
+  for (long long e = threadIdx.x; e < P; e += SPG_THREADS) {
+    const uint32_t ik = pidx[e];
+    const int i = ik >> 16, k = ik & 0xffff;
+    const double ve = vfull ? V[(size_t)i * m + k] : V[e];
+    const double f = i == k ? 1.0 : 2.0;
+    // U_e = f u_i u_k = uh + ul exactly
+    const double uh = f * (u[i] * u[k]);
+    const double ul = f * fma(u[i], u[k], -(u[i] * u[k]));
+    // A_0[e] U_e: error-free product of the high part, the low part rounded
+    const double ae = A0[e];
+    const double ph = ae * uh;
+    const double pl = fma(ae, uh, -ph) + ae * ul;
+    double es;
+    two_sum64(s, ph, s, es);
+    c += es + pl;
+    a = fma(fma(t0, ve, Y[e]), uh, a);
+    b = fma(ve, uh, b);
+  }
+  c += a;  // the small part joins the compensation term
+  const double num = block_sum_dd(s, c, red);
+  b = block_sum(b, red);
+  return b != 0.0 ? t0 - num / b : NAN;
 }
 
 // Pencil Rayleigh correction of a root t0 of det(F + tV) with null-vector

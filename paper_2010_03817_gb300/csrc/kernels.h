@@ -73,7 +73,7 @@ struct DevSpec {
 
 struct DevWork {
   double* Vfull;  // per CTA: m*m
-  double* Fg;     // per CTA: P
+  double* Fg;     // per CTA: P, Y = sum_{j>=1} p_j A_j of the current point (F = A_0 + Y)
   double* Q;      // per CTA: kmax*m
   double* Lg;     // per CTA: P (only when the factor does not fit in shared memory)
   int kmax;
@@ -250,10 +250,51 @@ cudaError_t launch_walk_fp64(const DevSpec& sp, const DevWork& wk, const WalkPar
 cudaError_t launch_prim_fp64(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
                              cudaStream_t st);
 
+// ---- a batch of spectrahedra in one persistent launch (FP64 path) ----------
+struct BatchBody {
+  DevSpec sp;
+  int l_in_smem;   // 1: the factor fits in shared memory
+  int panel;       // Cholesky panel width of this body (4, 8 or 16)
+  double tau;      // Billiard length scale
+  long long xoff;  // first double of the body's chain points in X
+  int c0;          // first global chain index (Philox chain, status, stats)
+  int C;           // chains of the body
+};
+struct BatchParams {
+  const BatchBody* bodies;
+  const int2* items;  // (body, chain within the body) in the order they are handed out
+  int total;
+  int* next;          // work-queue ticket (zero before the launch)
+  int steps;
+  uint32_t step0;
+  uint64_t seed;
+  double kappa, sigma_frac;
+  int rho;
+  double* X;          // all chains' points, body by body
+  int* status;        // total
+  long long* stats;   // total x kNumStats
+  // per-CTA work space sized for the largest body
+  double* Vfull;
+  double* Fg;
+  double* Q;
+  double* Lg;
+  long long max_mm, max_P;
+  int max_m, kmax;
+  double tol;
+};
+size_t batch_smem_bytes(int n, int m, bool l_in_smem);
+cudaError_t launch_batch_fp64(const BatchParams& bp, int ctas, size_t smem, cudaStream_t st);
+// REFLECTION of `count` lines with the Cholesky panel width `panel`, for the
+// panel tuner (FP64 path)
+cudaError_t launch_prim_fp64_panel(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
+                                   int panel, cudaStream_t st);
+DevSpec spec_dev(const sp_spec* s);
+
 // library internals for the host drivers (abi.cu): the packed LMI stack
 // ((n+1) x P doubles) copied to the host, and the device array of a chain
 // set's points (C x n)
 int spec_copy_stack(const sp_spec* s, double* packed_host);
 const double* chain_points(const sp_chains* ch);
+const double* chain_points(const sp_chains* ch, int* C, int* n);
 
 }  // namespace spg

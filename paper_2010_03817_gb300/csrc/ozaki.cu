@@ -136,13 +136,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(kGroups * kTileN <= 256, "the digit sums must fit the 256 TMEM columns");
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // a device-side row count (formation of a list built on the GPU): blocks
-  // past it leave before touching the tensor memory
+  // a device-side row count (formation of a list built on the GPU): rows
+  // from it on are skipped and blocks past it leave before touching the
+  // tensor memory.  R stays the stride of the digit planes (the slicing
+  // wrote plane s of row r at s R + r); Rl bounds the live rows.
+  int Rl = R;
   if (kMode == kForm && ep.count_dev) {
     const int rl = *ep.count_dev;
-    R = rl < R ? rl : R;
+    Rl = rl < R ? rl : R;
   }
-  if ((kMode == kForm ? (int)blockIdx.y : (int)blockIdx.x) * kTileM >= R) return;
+  if ((kMode == kForm ? (int)blockIdx.y : (int)blockIdx.x) * kTileM >= Rl) return;
   const int kgroups = Kp / 8;
   const uint32_t a_bytes = kTileM * Kp * 2;
   const uint32_t b_bytes = kTileN * Kp * 2;
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t base = sA_u[s & 1];
     int r = r_init, g = g_init;
     for (int q = tid; q < kTileM * kgroups; q += kThreads) {
-      const bool in = r0 + r < R;
+      const bool in = r0 + r < Rl;
       tc::cp_async16(base + core_off(r, g, kgroups),
                      in ? Asl + ((size_t)s * R + r0 + r) * Kp + g * 8 : Asl, in);
       r += dr;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::fence_after_sync();
   if (ok) {
     const int r = r0 + wid * 32 + lane;
-    const int er = (r < R) ? erow[r] : 0;
+    const int er = (r < Rl) ? erow[r] : 0;
     const uint32_t lane_base = tmem + ((uint32_t)(wid * 32) << 16);
     double part = 0.0;  // kContract
     const int jc = kMode == kContract ? (int)(p0 / ep.mpad) : 0;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           aux[i] = (ep.lead != 0.0 && p < P) ? ep.A0[p] : 0.0;
         } else {
           const int ii = i0 + c0 + i;
-          aux[i] = (r < R && ii < ep.m) ? ep.U[(size_t)r * ep.m + ii] : 0.0;
+          aux[i] = (r < Rl && ii < ep.m) ? ep.U[(size_t)r * ep.m + ii] : 0.0;
         }
       }
       long long hi[16], lo[16];
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             lo[i] = lo[i] * (1ll << kDigitBits) + g;
         }
       }
-      if (r < R) {
+      if (r < Rl) {
         if (kMode == kForm) {
           double* yrow = ep.Y + (size_t)(ep.rows ? ep.rows[r] : r) * ep.ldy;
 #pragma unroll
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (kMode == kContract && r < R)
+    if (kMode == kContract && r < Rl)
       ep.Wpart[((size_t)r * ep.n1 + jc) * (ep.mpad / kTileN) + i0 / kTileN] = part;
   }
   tc::fence_before_sync();

@@ -45,7 +45,7 @@ struct Smem {
 __host__ __device__ inline size_t align8(size_t b) { return (b + 7) & ~size_t(7); }
 
 // carve the dynamic shared memory
-__device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
+__device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg, int pw = kPanel) {
   Smem s;
   double* q = base;
   const long long P = (long long)m * (m + 1) / 2;
@@ -66,7 +66,7 @@ __device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
   s.ymax = q; q += m;
   s.ymin = q; q += m;
   s.u = q; q += m;
-  s.col = q; q += cholesky_scratch(m);
+  s.col = q; q += cholesky_scratch(m, pw);
   s.scr = q; q += SPG_SCR;
   s.bc = q; q += 16;
   s.sc = reinterpret_cast<LanczosScalars*>(q);
@@ -76,8 +76,21 @@ __device__ Smem carve(double* base, int n, int m, bool l_in_smem, double* Lg) {
   return s;
 }
 
+// The FP64 factorisation with a run-time panel width (one compiled copy per
+// width, called, so that the walk itself is compiled once)
+template <int PW>
+__device__ __noinline__ bool factor64_w(double* G, int m, double* pan, int* flag) {
+  return factor_cholesky<double, PW>(G, m, pan, flag);
+}
+__device__ __forceinline__ bool factor64(int pw, double* G, int m, double* pan, int* flag) {
+  if (pw == 4) return factor64_w<4>(G, m, pan, flag);
+  if (pw == 16) return factor64_w<16>(G, m, pan, flag);
+  return factor64_w<8>(G, m, pan, flag);
+}
+
 constexpr int kCdhrRefresh = 64;  // CDHR: steps between re-formations of F(p)
 constexpr double kRedoRatio = 100.0;  // |mu_min| / mu_max above which the solve is redone
+constexpr double kCorrectWindow = 1e-7;  // largest relative pencil correction kept
 
 struct SegResult {
   double t_plus, t_minus, t_raw;
@@ -93,7 +106,7 @@ struct SegResult {
 __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork& wk, Smem& sm,
                                   double* __restrict__ Vfull, double* __restrict__ Fg,
                                   double* __restrict__ Q, double sigma, bool want_min,
-                                  bool want_w, bool form_f, int vcol = -1) {
+                                  bool want_w, bool form_f, int vcol = -1, int PW = kPanel) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m;
   const long long P = sp.P;
@@ -108,7 +121,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
       double f;
       if (form_f) {
         const double* Ae = sp.A + e;
-        double f0 = Ae[0], f1 = 0.0;
+        double f0 = 0.0, f1 = 0.0;
         int j = 0;
         for (; j + 1 < n; j += 2) {
           f0 += sm.p[j] * Ae[(size_t)(j + 1) * P];
@@ -121,7 +134,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
         f = Fg[e];
       }
       const double g = Aj[e];
-      sm.L[e] = f + sigma * g;
+      sm.L[e] = fma(sigma, g, sp.A[e] + f);
       const uint32_t ik = sp.pidx[e];
       const int i = ik >> 16, k = ik & 0xffff;
       Vfull[(size_t)i * m + k] = g;
@@ -130,7 +143,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
   } else if (form_f) {
     for (long long e = tid; e < P; e += SPG_THREADS) {
       const double* Ae = sp.A + e;
-      double f0 = Ae[0], f1 = 0.0, g0 = 0.0, g1 = 0.0;
+      double f0 = 0.0, f1 = 0.0, g0 = 0.0, g1 = 0.0;
       int j = 0;
 #pragma unroll 4
       for (; j + 1 < n; j += 2) {
@@ -147,7 +160,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
       }
       const double f = f0 + f1, g = g0 + g1;
       Fg[e] = f;
-      sm.L[e] = f + sigma * g;
+      sm.L[e] = fma(sigma, g, Ae[0] + f);
       const uint32_t ik = sp.pidx[e];
       const int i = ik >> 16, k = ik & 0xffff;
       Vfull[(size_t)i * m + k] = g;
@@ -165,7 +178,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
       }
       if (j < n) g0 += sm.v[j] * Ae[(size_t)(j + 1) * P];
       const double g = g0 + g1;
-      sm.L[e] = Fg[e] + sigma * g;
+      sm.L[e] = fma(sigma, g, Ae[0] + Fg[e]);
       const uint32_t ik = sp.pidx[e];
       const int i = ik >> 16, k = ik & 0xffff;
       Vfull[(size_t)i * m + k] = g;
@@ -181,7 +194,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
   for (int attempt = 0;; ++attempt) {
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
-    bool ok = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+    bool ok = factor64(PW, sm.L, m, sm.col, &sm.ib[0]);
     if (ok) break;
     if (sigma != 0.0) {
       sigma = attempt < 3 ? 0.2 * sigma : 0.0;
@@ -189,7 +202,7 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
       res.flags |= kSegShiftRetry;
       for (long long e = tid; e < P; e += SPG_THREADS) {
         const uint32_t ik = sp.pidx[e];
-        sm.L[e] = Fg[e] + sigma * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+        sm.L[e] = fma(sigma, Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)], sp.A[e] + Fg[e]);
       }
       __syncthreads();
       continue;
@@ -226,11 +239,11 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
       const double s2 = sigma + 0.5 / lo.theta_max;
       for (long long e = tid; e < P; e += SPG_THREADS) {
         const uint32_t ik = sp.pidx[e];
-        sm.L[e] = Fg[e] + s2 * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+        sm.L[e] = fma(s2, Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)], sp.A[e] + Fg[e]);
       }
       if (tid == 0) sm.ib[0] = 0;
       __syncthreads();
-      const bool ok2 = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+      const bool ok2 = factor64(PW, sm.L, m, sm.col, &sm.ib[0]);
       if (ok2) {
         sigma = s2;
         res.flags |= kSegRefined;
@@ -238,11 +251,11 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
         // (the estimate overshot: back to the first factor)
         for (long long e = tid; e < P; e += SPG_THREADS) {
           const uint32_t ik = sp.pidx[e];
-          sm.L[e] = Fg[e] + sigma * Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)];
+          sm.L[e] = fma(sigma, Vfull[(size_t)(ik >> 16) * m + (ik & 0xffff)], sp.A[e] + Fg[e]);
         }
         if (tid == 0) sm.ib[0] = 0;
         __syncthreads();
-        factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+        factor64(PW, sm.L, m, sm.col, &sm.ib[0]);
       }
       invert_diag_blocks(sm.L, m);
       if (ok2) {
@@ -283,20 +296,24 @@ __device__ __noinline__ SegResult segment_fp64(const DevSpec& sp, const DevWork&
     for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] *= sc;
     __syncthreads();
   }
-  // both ends refined by the pencil Rayleigh correction on the exact F and V
-  // (Fg, Vfull), kept only when it is a correction of the Ritz value
-  {
-    const double tr =
-        pencil_correct(Fg, Vfull, true, m, P, sp.pidx, sm.u, res.t_plus, sm.sc->red);
-    if (tr > 0.0 && fabs(tr - res.t_plus) <= 1e-4 * res.t_plus) res.t_plus = tr;
+  // both ends of a converged solve refined by the pencil Rayleigh correction
+  // on the exact F = A_0 + Y and V (the A stack, Fg, Vfull).  The quotient
+  // never lies below the root (F + t+ V is semidefinite), so a correction is
+  // kept only while it stays within kCorrectWindow of the Ritz value, well
+  // inside the walk's backoff kappa: a larger one means an inaccurate u.
+  if (res.status == kOk) {
+    const double tr = pencil_correct_split(sp.A, Fg, Vfull, true, m, P, sp.pidx, sm.u,
+                                           res.t_plus, sm.scr);
+    if (tr > 0.0 && fabs(tr - res.t_plus) <= kCorrectWindow * res.t_plus) res.t_plus = tr;
   }
-  if (want_min && isfinite(res.t_minus)) {
+  if (res.status == kOk && want_min && isfinite(res.t_minus)) {
     for (int i = tid; i < m; i += SPG_THREADS) sm.z[i] = sm.ymin[i];
     __syncthreads();
     solve_upper(sm.L, sm.z, m, sm.scr);
-    const double tr =
-        pencil_correct(Fg, Vfull, true, m, P, sp.pidx, sm.z, res.t_minus, sm.sc->red);
-    if (tr < 0.0 && fabs(tr - res.t_minus) <= 1e-4 * fabs(res.t_minus)) res.t_minus = tr;
+    const double tr = pencil_correct_split(sp.A, Fg, Vfull, true, m, P, sp.pidx, sm.z,
+                                           res.t_minus, sm.scr);
+    if (tr < 0.0 && fabs(tr - res.t_minus) <= kCorrectWindow * fabs(res.t_minus))
+      res.t_minus = tr;
   }
   __syncthreads();
   if (!want_w) return res;
@@ -337,19 +354,15 @@ __device__ double unit_normal(const Smem& sm, int n, double* dst) {
   return nw;
 }
 
-__global__ void __launch_bounds__(SPG_THREADS, 1)
-    walk_fp64_kernel(DevSpec sp, DevWork wk, WalkParams wp) {
-  extern __shared__ double smem_raw[];
+// Every step of the walk `wp` for chain c (CTA-wide): wp.X, wp.status and
+// wp.stats are indexed by c, the Philox chain index is wp.chain0 + c; the
+// factor, V, F and the Lanczos basis live in sm / Vfull, Fg, Q.
+__device__ __noinline__ void walk_chain(const DevSpec& sp, const DevWork& wk,
+                                        const WalkParams& wp, Smem& sm, double* Vfull,
+                                        double* Fg, double* Q, int c, int PW = kPanel) {
   const int tid = threadIdx.x;
-  const int n = sp.n, m = sp.m;
-  const size_t cta = blockIdx.x;
-  double* Vfull = wk.Vfull + cta * (size_t)m * m;
-  double* Fg = wk.Fg + cta * (size_t)sp.P;
-  double* Q = wk.Q + cta * (size_t)wk.kmax * m;
-  double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
-  Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg);
-
-  for (int c = blockIdx.x; c < wp.C; c += gridDim.x) {
+  const int n = sp.n;
+  {
     double* xc = wp.X + (size_t)c * n;
     long long* st = wp.stats + (size_t)c * kNumStats;
     long long segs = 0, refl = 0, bad = 0, iters = 0, retries = 0, noconv = 0;
@@ -390,10 +403,11 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
         double sigma = 0.0;
         for (;;) {
           // F(p) is formed afresh with V on every segment (the formation loop
-          // reads the A stack once for both): an F carried through a long
-          // run of reflections accumulates the rounding of every update,
-          // which short chords next to the boundary amplify by |F| / |u^T V u|
-          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true, true);
+          // reads the A stack once for both), as A_0 + Y with Y = sum p_j A_j
+          // kept apart: an F carried through a long run of reflections
+          // accumulates the rounding of every update, which short chords next
+          // to the boundary amplify by |F| / |u^T V u|
+          SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, sigma, false, true, true, -1, PW);
           ++segs;
           iters += r.iters;
           retries += r.retried;
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
           for (int j = 0; j < n; ++j)
             if (sm.v[j] != 0.0) jc = j;
         const bool form = !cd || k % kCdhrRefresh == 0;
-        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false, form, jc);
+        SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, true, false, form, jc, PW);
         ++segs;
         iters += r.iters;
         if (r.status == kNoConv) {
@@ -510,7 +524,21 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
 }
 
 __global__ void __launch_bounds__(SPG_THREADS, 1)
-    prim_fp64_kernel(DevSpec sp, DevWork wk, PrimParams pp) {
+    walk_fp64_kernel(DevSpec sp, DevWork wk, WalkParams wp) {
+  extern __shared__ double smem_raw[];
+  const int m = sp.m;
+  const size_t cta = blockIdx.x;
+  double* Vfull = wk.Vfull + cta * (size_t)m * m;
+  double* Fg = wk.Fg + cta * (size_t)sp.P;
+  double* Q = wk.Q + cta * (size_t)wk.kmax * m;
+  double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
+  Smem sm = carve(smem_raw, sp.n, m, wk.l_in_smem, Lg);
+  for (int c = blockIdx.x; c < wp.C; c += gridDim.x)
+    walk_chain(sp, wk, wp, sm, Vfull, Fg, Q, c);
+}
+
+__global__ void __launch_bounds__(SPG_THREADS, 1)
+    prim_fp64_kernel(DevSpec sp, DevWork wk, PrimParams pp, int PW) {
   extern __shared__ double smem_raw[];
   const int tid = threadIdx.x;
   const int n = sp.n, m = sp.m;
@@ -519,7 +547,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   double* Fg = wk.Fg + cta * (size_t)sp.P;
   double* Q = wk.Q + cta * (size_t)wk.kmax * m;
   double* Lg = wk.l_in_smem ? nullptr : wk.Lg + cta * (size_t)sp.P;
-  Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg);
+  Smem sm = carve(smem_raw, n, m, wk.l_in_smem, Lg, PW);
   for (int c = blockIdx.x; c < pp.count; c += gridDim.x) {
     double bad = 0.0;
     for (int j = tid; j < n; j += SPG_THREADS) {
@@ -552,12 +580,12 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
       }
       if (tid == 0) sm.ib[0] = 0;
       __syncthreads();
-      bool ok = factor_cholesky(sm.L, m, sm.col, &sm.ib[0]);
+      bool ok = factor64(PW, sm.L, m, sm.col, &sm.ib[0]);
       if (tid == 0) pp.inside[c] = ok ? 1 : 0;
       __syncthreads();
       continue;
     }
-    SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, pp.op == 0, true, true);
+    SegResult r = segment_fp64(sp, wk, sm, Vfull, Fg, Q, 0.0, pp.op == 0, true, true, -1, PW);
     int status = r.status;
     if (pp.op == 0) {
       if (tid == 0) {
@@ -592,7 +620,86 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   }
 }
 
+// The walks of a batch of spectrahedra of uneven n and m in one persistent
+// launch: every block takes the next (body, chain) item from the queue (items
+// in decreasing order of estimated cost, so the longest ones start first and
+// the tail is short), carves its shared memory for that body's n and m, and
+// runs all the steps of that chain with the body's Cholesky panel width.
+__global__ void __launch_bounds__(SPG_THREADS, 1) batch_fp64_kernel(BatchParams bp) {
+  extern __shared__ double smem_raw[];
+  __shared__ int ticket;
+  const size_t cta = blockIdx.x;
+  for (;;) {
+    if (threadIdx.x == 0) ticket = atomicAdd(bp.next, 1);
+    __syncthreads();
+    const int it = ticket;
+    __syncthreads();
+    if (it >= bp.total) break;
+    const int2 item = bp.items[it];
+    const BatchBody B = bp.bodies[item.x];
+    DevWork wk;
+    wk.Vfull = bp.Vfull + cta * (size_t)bp.max_mm;
+    wk.Fg = bp.Fg + cta * (size_t)bp.max_P;
+    wk.Q = bp.Q + cta * (size_t)bp.kmax * bp.max_m;
+    wk.Lg = B.l_in_smem ? nullptr : bp.Lg + cta * (size_t)bp.max_P;
+    wk.kmax = bp.kmax;
+    wk.tol = bp.tol;
+    wk.l_in_smem = B.l_in_smem;
+    wk.ctas = gridDim.x;
+    Smem sm = carve(smem_raw, B.sp.n, B.sp.m, B.l_in_smem, wk.Lg, kMaxPanel);
+    WalkParams wp{};
+    wp.kind = 0;
+    wp.C = B.C;
+    wp.steps = bp.steps;
+    wp.step0 = bp.step0;
+    wp.chain0 = (uint32_t)B.c0;
+    wp.seed = bp.seed;
+    wp.tau = B.tau;
+    wp.kappa = bp.kappa;
+    wp.sigma_frac = bp.sigma_frac;
+    wp.rho = bp.rho;
+    wp.X = bp.X + B.xoff;
+    wp.status = bp.status + B.c0;
+    wp.stats = bp.stats + (size_t)B.c0 * kNumStats;
+    wp.seg = SegLog{nullptr, 0, 1, nullptr};
+    __syncthreads();
+    walk_chain(B.sp, wk, wp, sm, wk.Vfull, wk.Fg, wk.Q, item.y, B.panel);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+size_t batch_smem_bytes(int n, int m, bool l_in_smem) {
+  const size_t P = (size_t)m * (m + 1) / 2;
+  size_t d = (l_in_smem ? P : 0) + 4 * (size_t)n + (n + 1) + 6 * (size_t)m +
+             cholesky_scratch(m, kMaxPanel) + SPG_SCR + 16;
+  return d * 8 + align8(sizeof(LanczosScalars)) + 16 * sizeof(int);
+}
+
+cudaError_t launch_batch_fp64(const BatchParams& bp, int ctas, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(batch_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (ctas <= 0 || bp.total <= 0) return cudaSuccess;
+  batch_fp64_kernel<<<ctas, SPG_THREADS, smem, st>>>(bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_fp64_panel(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
+                                   int panel, cudaStream_t st) {
+  const int pw = panel == 4 ? 4 : (panel == 16 ? 16 : 8);
+  // the default kernel's shared memory with the scratch of this panel width
+  const size_t smem = fp64_smem_bytes(sp.n, sp.m, wk.l_in_smem) + 8 * cholesky_scratch(sp.m, pw) -
+                      8 * cholesky_scratch(sp.m);
+  cudaError_t e = cudaFuncSetAttribute(prim_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = pp.count < wk.ctas ? pp.count : wk.ctas;
+  if (grid <= 0) return cudaSuccess;
+  prim_fp64_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wk, pp, pw);
+  return cudaGetLastError();
+}
 
 size_t fp64_smem_bytes(int n, int m, bool l_in_smem) {
   const size_t P = (size_t)m * (m + 1) / 2;
@@ -622,7 +729,7 @@ cudaError_t launch_prim_fp64(const DevSpec& sp, const DevWork& wk, const PrimPar
   if (e != cudaSuccess) return e;
   const int grid = pp.count < wk.ctas ? pp.count : wk.ctas;
   if (grid <= 0) return cudaSuccess;
-  prim_fp64_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wk, pp);
+  prim_fp64_kernel<<<grid, SPG_THREADS, smem, st>>>(sp, wk, pp, kPanel);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,16 @@ def _bind(L):
     f("sp_record_segments", [_vp, _vp, _i, _i, _vp])
     f("sp_learned_counts", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
     f("sp_selftest_recip", [_i, _vp, _vp, _vp])
+    f("sp_halfspace_fraction", [_vp, _vp, _d, _d, _i, _vp, _vp])
+    f("sp_create_batch", [_i, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(_vp), _vp])
+    f("sp_destroy_batch", [_vp])
+    f("sp_batch_billiard", [_vp, _i, _vp, _i, _d, _vp])
+    f("sp_batch_dims", [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                        ctypes.POINTER(_i)])
+    f("sp_batch_state", [_vp, _i, _vp, ctypes.POINTER(ctypes.c_uint32), _vp])
+    f("sp_batch_stats", [_vp, _vp, _vp])
+    f("sp_batch_panels", [_vp, _vp, _vp])
+    f("sp_batch_tune", [_vp, ctypes.c_char_p, _vp, _vp])
     f("sp_mlp_create", [_i, _i, _i, ctypes.c_uint64, ctypes.POINTER(_vp)])
     f("sp_mlp_destroy", [_vp])
     f("sp_mlp_dims", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -177,17 +187,18 @@ def version() -> str:
 class Spectrahedron:
     """Device-resident LMI F(x) = A_0 + sum_i x_i A_i (Eq. 1).
 
-    A: (n+1, m, m) float64 array-like on the host."""
+    A: (n+1, m, m) float64 array-like on the host; fp64_only skips the mixed
+    path's precomputed operands (SP_FLAG_FP64_ONLY)."""
 
-    def __init__(self, A):
+    def __init__(self, A, fp64_only: bool = False):
         A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
         if A.ndim != 3 or A.shape[1] != A.shape[2]:
             raise ValueError("A must be (n+1) x m x m")
         self.n = A.shape[0] - 1
         self.m = A.shape[1]
         h = _vp()
-        _check(lib().sp_create_spectrahedron(self.n, self.m, A.ctypes.data_as(_vp), 0,
-                                             ctypes.byref(h)))
+        _check(lib().sp_create_spectrahedron(self.n, self.m, A.ctypes.data_as(_vp),
+                                             1 if fp64_only else 0, ctypes.byref(h)))
         self._h = h
 
     @property
@@ -392,6 +403,17 @@ class Chains:
         _check(lib().sp_record_tuples(self._h, _dev(x_out, torch.float32), _dev(y_out, torch.float32),
                                       cap, _dev(count, torch.int32)))
 
+    def halfspace_fraction(self, c, b1: float, b2: float, groups: int = 1, stream=None):
+        """Per group of C / groups chains, the fraction of points with
+        c.x <= b1 or c.x >= b2 (sp_halfspace_fraction); c: host array (n)."""
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+        if c.shape != (self.spec.n,):
+            raise ValueError("c must have n entries")
+        out = np.zeros(groups, dtype=np.float64)
+        _check(lib().sp_halfspace_fraction(self._h, c.ctypes.data_as(_vp), b1, b2, groups,
+                                           out.ctypes.data_as(_vp), _stream(stream)))
+        return out
+
     def record_segments(self, buf=None, count=None, every: int = 1):
         """Record every `every`-th boundary-oracle call of later walks into buf
         (CUDA float64 tensor, capacity x (3n + 8)) with the int32 ticket
@@ -413,6 +435,76 @@ class Chains:
         stats = (ctypes.c_longlong * NUM_STATS)()
         _check(lib().sp_chain_status(self._h, _dev(st), stats, _stream(stream)))
         return st, {k: int(stats[i]) for i, k in enumerate(STAT_NAMES)}
+
+
+class Batch:
+    """Spectrahedra of uneven sizes walked together in one persistent launch
+    (sp_create_batch / sp_batch_*; FP64 path).  specs: Spectrahedron objects
+    (kept alive by the batch); chains: chains per body (start: the origin)."""
+
+    def __init__(self, specs, chains, seed: int = 0, stream=None):
+        self.specs = list(specs)
+        self.B = len(self.specs)
+        hs = (_vp * self.B)(*[sp.handle for sp in self.specs])
+        cs = np.ascontiguousarray(np.asarray(chains, dtype=np.int32))
+        h = _vp()
+        _check(lib().sp_create_batch(self.B, ctypes.cast(hs, _vp), cs.ctypes.data_as(_vp), seed,
+                                     ctypes.byref(h), _stream(stream)))
+        self._h = h
+        self.chains = cs.tolist()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sp_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def billiard(self, steps: int, tau, rho: int = 100, kappa: float = 1e-6, stream=None):
+        t = np.ascontiguousarray(np.asarray(tau, dtype=np.float64).reshape(-1))
+        if t.size == 1:
+            t = np.full(self.B, float(t[0]))
+        _check(lib().sp_batch_billiard(self._h, steps, t.ctypes.data_as(_vp), rho, kappa,
+                                       _stream(stream)))
+
+    def dims(self, body: int):
+        n, m, c, c0 = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().sp_batch_dims(self._h, body, ctypes.byref(n), ctypes.byref(m),
+                                   ctypes.byref(c), ctypes.byref(c0)))
+        return n.value, m.value, c.value, c0.value
+
+    def state(self, body: int, stream=None) -> np.ndarray:
+        n, _, c, _ = self.dims(body)
+        out = np.empty((c, n), dtype=np.float64)
+        _check(lib().sp_batch_state(self._h, body, out.ctypes.data_as(_vp), None,
+                                    _stream(stream)))
+        return out
+
+    def stats(self, stream=None):
+        out = np.zeros((self.B, NUM_STATS), dtype=np.int64)
+        _check(lib().sp_batch_stats(self._h, out.ctypes.data_as(_vp), _stream(stream)))
+        return [{k: int(out[b, i]) for i, k in enumerate(STAT_NAMES)} for b in range(self.B)]
+
+    def panels(self, new=None):
+        out = np.zeros(self.B, dtype=np.int32)
+        p_in = None
+        if new is not None:
+            p_in = np.ascontiguousarray(np.asarray(new, dtype=np.int32))
+        _check(lib().sp_batch_panels(self._h, out.ctypes.data_as(_vp),
+                                     p_in.ctypes.data_as(_vp) if p_in is not None else None))
+        return out
+
+    def tune(self, cache_path=None, stream=None):
+        """Autotune the Cholesky panel width per body (sp_batch_tune);
+        returns (panels, calibration ms per width 4/8/16)."""
+        times = np.zeros((self.B, 3), dtype=np.float64)
+        _check(lib().sp_batch_tune(self._h, os.fsencode(cache_path) if cache_path else None,
+                                   times.ctypes.data_as(_vp), _stream(stream)))
+        return self.panels(), times
 
 
 class MLP:
