@@ -109,6 +109,9 @@ def lib():
             L.orc_reflect_batch.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
                                             _dp, _dp, _dp, _dp, _i32p, _dp]
             L.orc_reflect_batch.restype = None
+            L.orc_intersect_batch.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                              _dp, _dp, _dp, _i32p]
+            L.orc_intersect_batch.restype = None
             _lib = L
     return _lib
 
@@ -312,6 +315,19 @@ def reflect_batch(A, P, V) -> dict:
     lib().orc_reflect_batch(n, m, _d(A), cnt, _d(P), _d(V), _d(tp), _d(wh), _d(s),
                             st.ctypes.data_as(_i32p), _d(info))
     return dict(status=st, t_plus=tp, w_hat=wh, s=s, err_bar=info[:, 0], rel_gap=info[:, 1])
+
+
+def intersect_batch(A, P, V) -> dict:
+    """intersect() (t-, t+, status) on every line (P[c], V[c]), in parallel."""
+    A, n, m = _stack(A)
+    P, V = _f64(P), _f64(V)
+    cnt = P.shape[0]
+    tm = np.zeros(cnt)
+    tp = np.zeros(cnt)
+    st = np.zeros(cnt, dtype=np.int32)
+    lib().orc_intersect_batch(n, m, _d(A), cnt, _d(P), _d(V), _d(tm), _d(tp),
+                              st.ctypes.data_as(_i32p))
+    return dict(status=st, t_minus=tm, t_plus=tp)
 
 
 def num_threads() -> int:

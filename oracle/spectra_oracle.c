@@ -618,6 +618,21 @@ void orc_billiard_trace(int n, int m, const double* A, int C, double* X, uint32_
 }
 
 /*
+ * orc_intersect on `count` independent lines (rows of P and V, count x n):
+ * t_minus[c], t_plus[c], status[c] (in parallel with OpenMP).
+ */
+void orc_intersect_batch(int n, int m, const double* A, int count, const double* P,
+                         const double* V, double* t_minus, double* t_plus, int* status) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < count; ++c) {
+    t_minus[c] = 0.0;
+    t_plus[c] = 0.0;
+    status[c] = orc_intersect(n, m, A, P + (size_t)c * n, V + (size_t)c * n, t_minus + c,
+                              t_plus + c, NULL, NULL, NULL, NULL);
+  }
+}
+
+/*
  * orc_reflect on `count` independent lines (p_c, v_c) (rows of P and V,
  * count x n): t_plus[c], w_hat (count x n), status[c] and info (count x 4, the
  * per-line info of orc_intersect).  Lines run in parallel (OpenMP).

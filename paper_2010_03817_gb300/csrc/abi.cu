@@ -215,7 +215,7 @@ struct sp_spec {
   uint16_t* Bc = nullptr;  // digits of the rows (j, i) of A_j: tensor-core normals
   int* ecolc = nullptr;
   int kmax32 = 96, kmax64 = 96, power_iters = 8;
-  double tol32 = 1e-4, tol64 = 1e-12, delta1 = 2e-4;
+  double tol32 = 1e-4, tol64 = 1e-10, delta1 = 2e-4;
   long long* prof = nullptr;  // optional stage timers (device, ctas x kProfSlots)
   int learned_iters = 12;
   // learned warm start

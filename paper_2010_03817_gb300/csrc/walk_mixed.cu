@@ -27,6 +27,9 @@
 namespace spg {
 namespace {
 
+constexpr int kStage2Panel = 16;  // panel width of the double-float factorisation
+static_assert(kStage2Panel <= kMaxPanel, "the panel scratch holds up to kMaxPanel columns");
+
 struct MixSmem {
   uint8_t* R;     // region: stage 1 (G32, V32), stage 2 (G64), stage 3 (U hi, lo)
   double* p;      // n
@@ -77,7 +80,7 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.z = d; d += m;
   s.u = d; d += m;
   s.um = d; d += m;
-  s.part = d; d += (size_t)SPG_WARPS * m + 64;  // also the Cholesky panel
+  s.part = d; d += (size_t)SPG_WARPS * m + 128;  // also the Cholesky panel (up to 16 wide)
   s.scr = d; d += SPG_SCR;
   s.bc = d; d += 16;
   float* f = reinterpret_cast<float*>(d);
@@ -307,7 +310,9 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
     }
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
-    ok = factor_cholesky<T>(G, m, part, &sm.ib[0]);
+    // 16-column panels: half the barrier rounds of the default width for the
+    // factorisation that dominates the segment
+    ok = factor_cholesky<T, kStage2Panel>(G, m, part, &sm.ib[0]);
     if (!ok) {
       ++res->retries;
       delta *= 8.0;
@@ -962,8 +967,11 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
     const double sigma0 = (wv.kind == 0 && nrefl > 0) ? mw.sigma_frac * tprev : 0.0;
     const float* prow =
         (wv.pred && wv.kind == 0) ? wv.pred + (size_t)r * wv.ld_pred : nullptr;
-    MixResult res = segment_mixed(sp, mw, sm, Fc, Vr, Q32, Q64, sigma0, wv.kind != 0,
-                                  wv.kind == 0, prow, wv.t_scale, wv.margin);
+    // every walk refines its roots next to the boundary (stage 2): the chord
+    // walks both ends, since a uniform point of a chord whose end is off by
+    // the FP32 estimate's error can leave S
+    MixResult res = segment_mixed(sp, mw, sm, Fc, Vr, Q32, Q64, sigma0, wv.kind != 0, true,
+                                  prow, wv.t_scale, wv.margin);
     if (wv.rec_x && wv.kind == 0 && res.status == kOk && isfinite(res.t_plus)) {
       // training tuple: (x * x_scale, v) -> (log(t+ / t_scale), u)
       if (tid == 0) sm.ib[2] = atomicAdd(wv.rec_count, 1);
@@ -1254,7 +1262,7 @@ size_t mixed_region_bytes(int n, int m) {
 
 size_t mixed_smem_bytes(int n, int m, bool region_in_smem) {
   size_t b = region_in_smem ? ((mixed_region_bytes(n, m) + 15) & ~size_t(15)) : 0;
-  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 64 + SPG_SCR + 16);
+  b += 8 * ((size_t)4 * n + 1 + 5 * (size_t)m + (size_t)SPG_WARPS * m + 128 + SPG_SCR + 16);
   b += 4 * (size_t)12 * m;
   b += sizeof(LanczosScalars) + 16 * sizeof(int);
   return b;

@@ -238,7 +238,7 @@ class Spectrahedron:
     def set_solver(self, kmax: int = 96, tol: float = 1e-13, sigma_frac: float = 0.1):
         _check(lib().sp_set_solver(self._h, kmax, tol, sigma_frac))
 
-    def set_mixed_solver(self, tol32: float = 1e-4, tol64: float = 1e-12, delta1: float = 2e-4,
+    def set_mixed_solver(self, tol32: float = 1e-4, tol64: float = 1e-10, delta1: float = 2e-4,
                          power_iters: int = 8):
         """Stage-1 / stage-2 parameters of the mixed path (sp_set_mixed_solver)."""
         _check(lib().sp_set_mixed_solver(self._h, tol32, tol64, delta1, power_iters))

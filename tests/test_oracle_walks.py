@@ -161,3 +161,16 @@ def test_reflect_batch_equals_single_calls():
         assert rb["t_plus"][c] == r["t_plus"]
         assert np.array_equal(rb["w_hat"][c], r["w_hat"])
         assert rb["rel_gap"][c] == r["rel_gap"]
+
+
+def test_intersect_batch_equals_single_calls():
+    n = 4
+    A = W.ball_random(n, 3, 2.0, seed=W.BASE_SEED + 42)
+    g = np.random.default_rng(5)
+    P = g.uniform(-0.2, 0.2, size=(6, n))
+    V = W.random_directions(n, 6, seed=6)
+    rb = oracle.intersect_batch(A, P, V)
+    for c in range(6):
+        r = oracle.intersect(A, P[c], V[c])
+        assert rb["status"][c] == r["status"]
+        assert rb["t_plus"][c] == r["t_plus"] and rb["t_minus"][c] == r["t_minus"]
