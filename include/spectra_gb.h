@@ -182,6 +182,42 @@ int sp_step_hnr(sp_chains* ch, int steps, int mode, void* stream);
 int sp_step_cdhr(sp_chains* ch, int steps, int mode, void* stream);
 
 /*
+ * REFLECTION on the trajectories of HMC for the Boltzmann density
+ * pi(x) ~ exp(-c.x / T) (Sec. 3.3, Alg. 6; FP64; m <= 64).  For f(x) = c.x / T
+ * the Hamiltonian ODE has the exact solution Phi(t) = x + v t - (c / (2T)) t^2,
+ * so F(Phi(t)) = F(x) + t V + t^2 C (V = sum v_j A_j, C = -(1/(2T)) sum c_j A_j),
+ * a quadratic eigenvalue problem (Sec. 2.1) solved through its companion
+ * linearisation of size 2m: t_plus[k] is its first positive root (+inf and
+ * SP_ST_UNBOUNDED when there is none), w_hat the unit normal w / |w|,
+ * w_j = u^T A_j u at Phi(t_plus) (pointing into S), s the velocity
+ * Phi'(t_plus) = v - (c / T) t_plus reflected on it:
+ * s = Phi' - 2 <Phi', w_hat> w_hat (Sec. 2.4).
+ *   x, v: device, count x n (start points, interior; initial velocities).
+ *   c: host or device, n.  T > 0.
+ *   t_plus: device, count.  w_hat, s: device, count x n (zero unless status
+ *   is SP_ST_OK).  status: device int32, count (SP_ST_NOTPD for a start
+ *   outside S, SP_ST_NOCONV when the eigenvalue iteration hits its cap).
+ * Errors: SP_EINVAL for m > 64, count < 0, T <= 0 or a NULL argument.
+ */
+int sp_curve_reflect(sp_spec* s, int count, const double* x, const double* v, const double* c,
+                     double T, double* t_plus, double* w_hat, double* s_out, int* status,
+                     void* stream);
+
+/*
+ * HMC with reflections (Sec. 3.3, Alg. 6) for pi(x) ~ exp(-c.x / T): `steps`
+ * steps on every chain (FP64; m <= 64).  Each step draws the momentum
+ * v ~ N(0, I_n) (Philox stream 0, not normalised) and the length
+ * l = tau eta (eta uniform, stream 1), then follows Phi from the chain's
+ * point, reflecting (as sp_curve_reflect) until l is used up; after a hit
+ * at t+ the walker moves to Phi((1 - kappa) t+) and the remaining length
+ * drops by t+.  A step with more than rho reflections, or whose boundary
+ * oracle fails, keeps its start point (status as sp_step_billiard).
+ *   c: host or device, n.  T, tau > 0, rho >= 0, 0 <= kappa < 1.
+ */
+int sp_step_hmc(sp_chains* ch, int steps, const double* c, double T, double tau, int rho,
+                double kappa, void* stream);
+
+/*
  * Volume of S by multiphase Monte Carlo over a sequence of balls (Sec. 4.1,
  * the multiphase scheme with the Billiard walk): radii r_0 = r_inner < r_1 <
  * ... < r_q = r_outer, geometric, q = ceil(n ln(r_outer / r_inner) / ln(1 /

@@ -319,6 +319,22 @@ int spec_copy_stack(const sp_spec* s, double* packed_host) {
   return SP_OK;
 }
 DevSpec spec_dev(const sp_spec* s) { return s->dev(); }
+ChainState chain_state(sp_chains* ch) {
+  ChainState c;
+  c.X = ch->X;
+  c.status = ch->status;
+  c.stats = ch->stats;
+  c.C = ch->C;
+  c.seed = ch->seed;
+  c.chain0 = ch->chain0;
+  c.step = ch->step;
+  c.spec = ch->spec;
+  return c;
+}
+void chain_advance(sp_chains* ch, uint32_t steps) {
+  ch->step += steps;
+  ch->F_valid = false;
+}
 const double* chain_points(const sp_chains* ch) { return ch->X; }
 const double* chain_points(const sp_chains* ch, int* C, int* n) {
   *C = ch->C;

@@ -289,6 +289,44 @@ cudaError_t launch_batch_fp64(const BatchParams& bp, int ctas, size_t smem, cuda
 cudaError_t launch_prim_fp64_panel(const DevSpec& sp, const DevWork& wk, const PrimParams& pp,
                                    int panel, cudaStream_t st);
 DevSpec spec_dev(const sp_spec* s);
+// a chain set's device state for walk drivers outside abi.cu
+struct ChainState {
+  double* X;
+  int* status;
+  long long* stats;
+  int C;
+  uint64_t seed;
+  uint32_t chain0, step;
+  sp_spec* spec;
+};
+ChainState chain_state(sp_chains* ch);
+void chain_advance(sp_chains* ch, uint32_t steps);  // the step counter moves on
+
+// ---- HMC with reflections on the degree-2 Boltzmann trajectory (hmc.cu) ----
+struct CurveParams {
+  int op;            // 0 reflect lines (primitive), 1 walk
+  int count;         // lines (op 0) or chains (op 1)
+  const double* x;   // op 0: count x n start points
+  const double* v;   // op 0: count x n initial velocities
+  const double* c;   // n: the Boltzmann density's linear coefficient
+  const double* Cp;  // P: packed C = -(1/(2T)) sum c_j A_j
+  double T;
+  double* t_plus;    // op 0
+  double* w_hat;     // op 0: count x n
+  double* s;         // op 0: count x n
+  int* status;       // count
+  // walk (op 1)
+  double* X;
+  long long* stats;
+  int steps;
+  uint32_t step0, chain0;
+  uint64_t seed;
+  double tau, kappa;
+  int rho;
+};
+size_t curve_smem_bytes(int n, int m);
+cudaError_t launch_curve(const DevSpec& sp, const CurveParams& cp, int ctas, cudaStream_t st);
+constexpr int kCurveMaxM = 64;  // the companion matrix (2m x 2m) lives in shared memory
 
 // library internals for the host drivers (abi.cu): the packed LMI stack
 // ((n+1) x P doubles) copied to the host, and the device array of a chain

@@ -76,6 +76,8 @@ def _bind(L):
     f("sp_learned_counts", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
     f("sp_selftest_recip", [_i, _vp, _vp, _vp])
     f("sp_halfspace_fraction", [_vp, _vp, _d, _d, _i, _vp, _vp])
+    f("sp_curve_reflect", [_vp, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp])
+    f("sp_step_hmc", [_vp, _i, _vp, _d, _d, _i, _d, _vp])
     f("sp_create_batch", [_i, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(_vp), _vp])
     f("sp_destroy_batch", [_vp])
     f("sp_batch_billiard", [_vp, _i, _vp, _i, _d, _vp])
@@ -310,6 +312,27 @@ class Spectrahedron:
                                 _dev(s), _dev(st), MODES[mode], _stream(stream)))
         return tp, wh, s, st
 
+    def curve_reflect(self, x, v, c, T: float, stream=None):
+        """REFLECTION of the HMC trajectories x_c + v_c t - (c / (2T)) t^2 of
+        the Boltzmann density exp(-c.x / T) (Sec. 3.3; m <= 64):
+        (t_plus, w_hat, s, status), s the reflected velocity at the hit point;
+        c: host array (n)."""
+        import torch
+        C = x.shape[0]
+        dev = x.device
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+        if c.shape != (self.n,):
+            raise ValueError("c must have n entries")
+        tp = torch.empty(C, dtype=torch.float64, device=dev)
+        wh = torch.empty((C, self.n), dtype=torch.float64, device=dev)
+        s = torch.empty((C, self.n), dtype=torch.float64, device=dev)
+        st = torch.empty(C, dtype=torch.int32, device=dev)
+        _check(lib().sp_curve_reflect(self._h, C, _dev(x, torch.float64, (C, self.n), "x"),
+                                      _dev(v, torch.float64, (C, self.n), "v"),
+                                      c.ctypes.data_as(_vp), T, _dev(tp), _dev(wh), _dev(s),
+                                      _dev(st), _stream(stream)))
+        return tp, wh, s, st
+
 
 class Chains:
     """C independent walkers on a Spectrahedron (state on the device)."""
@@ -355,6 +378,15 @@ class Chains:
 
     def cdhr(self, steps: int, mode: str = "fp64", stream=None):
         _check(lib().sp_step_cdhr(self._h, steps, MODES[mode], _stream(stream)))
+
+    def hmc(self, steps: int, c, T: float, tau: float, rho: int = 100, kappa: float = 1e-6,
+            stream=None):
+        """HMC with reflections for exp(-c.x / T) (Alg. 6, sp_step_hmc); c: host array (n)."""
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+        if c.shape != (self.spec.n,):
+            raise ValueError("c must have n entries")
+        _check(lib().sp_step_hmc(self._h, steps, c.ctypes.data_as(_vp), T, tau, rho, kappa,
+                                 _stream(stream)))
 
     def state(self, stream=None):
         """(x as a CUDA float64 tensor (C, n), next step number)."""

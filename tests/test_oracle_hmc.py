@@ -1,0 +1,106 @@
+"""Pins of the HMC oracle (the degree-2 trajectory of Alg. 6 for the
+Boltzmann density) against what the geometry fixes without it:
+
+* c = 0: the trajectory is the line, and every output equals the line
+  oracle's REFLECTION (a different code path: Jacobi on the linear pencil).
+* The rotated cube [-1, 1]^n: Phi_i(t) = p_i + v_i t - c_i t^2 / (2T) meets a
+  face where a scalar quadratic vanishes; the first root over all faces is
+  t+, the face normal is -+e_i (pointing inward) and the reflection flips
+  the i-th component of the velocity Phi'(t+).
+* The ball |x| <= r: |Phi(t)|^2 = r^2 is a quartic in t (library roots); the
+  normal at the hit point q is -q/|q|.
+* The walk keeps every point inside and follows the trajectory it states.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hmc
+from paper_2010_03817_gb300 import workloads as W
+
+
+def _first_root_cube(p, v, c, T):
+    best, face = np.inf, None
+    a2 = -c / (2 * T)
+    for i in range(len(p)):
+        for sgn in (1.0, -1.0):
+            # p_i + v_i t + a2_i t^2 = sgn
+            r = np.roots([a2[i], v[i], p[i] - sgn]) if a2[i] != 0 else np.array(
+                [(sgn - p[i]) / v[i]] if v[i] != 0 else [])
+            for t in np.atleast_1d(r):
+                if abs(np.imag(t)) == 0 and np.real(t) > 1e-14 and np.real(t) < best:
+                    best, face = float(np.real(t)), (i, sgn)
+    return best, face
+
+
+def test_line_limit_equals_the_line_oracle():
+    A = W.ball_random(5, 4, 2.0, seed=W.BASE_SEED + 80)
+    g = np.random.default_rng(1)
+    for _ in range(4):
+        p = g.uniform(-0.2, 0.2, 5)
+        v = W.random_directions(5, 1, seed=int(g.integers(1 << 30)))[0]
+        r = hmc.curve_reflect(A, p, v, np.zeros(5), 1.0)
+        ro = oracle.reflect(A, p, v)
+        assert r["status"] == 0 and ro["status"] == 0
+        assert abs(r["t_plus"] - ro["t_plus"]) <= 1e-12 * ro["t_plus"]
+        assert np.allclose(r["w_hat"], ro["w_hat"], atol=1e-10)
+        assert np.allclose(r["s"], ro["s"], atol=1e-10)
+
+
+@pytest.mark.parametrize("T", [0.3, 1.0, 5.0])
+def test_cube_closed_form(T):
+    n = 4
+    A = W.rotated_cube(n, seed=W.BASE_SEED + 81)
+    g = np.random.default_rng(2)
+    for _ in range(6):
+        p = g.uniform(-0.8, 0.8, n)
+        v = g.normal(size=n)
+        c = g.normal(size=n)
+        t_ref, (i, sgn) = _first_root_cube(p, v, c, T)
+        roots = hmc.curve_roots(A, p, v, c, T)
+        assert abs(roots[0] - t_ref) <= 1e-9 * t_ref
+        r = hmc.curve_reflect(A, p, v, c, T)
+        assert abs(r["t_plus"] - t_ref) <= 1e-12 * t_ref
+        e = np.zeros(n)
+        e[i] = -sgn
+        assert np.allclose(r["w_hat"], e, atol=1e-9)
+        vel = v - c / T * t_ref
+        s_ref = vel.copy()
+        s_ref[i] = -vel[i]
+        assert np.allclose(r["s"], s_ref, atol=1e-9)
+
+
+def test_ball_quartic():
+    n, R, T = 5, 1.5, 0.7
+    A = W.ball(n, R)
+    g = np.random.default_rng(3)
+    for _ in range(6):
+        p = g.uniform(-0.4, 0.4, n)
+        v = g.normal(size=n)
+        c = g.normal(size=n) * 2.0
+        a = -c / (2 * T)
+        coef = [a @ a, 2 * (v @ a), v @ v + 2 * (p @ a), 2 * (p @ v), p @ p - R * R]
+        rr = np.roots(coef)
+        t_ref = min(float(np.real(t)) for t in rr if abs(np.imag(t)) < 1e-12 and np.real(t) > 0)
+        r = hmc.curve_reflect(A, p, v, c, T)
+        assert abs(r["t_plus"] - t_ref) <= 1e-10 * t_ref
+        q = p + v * t_ref + a * t_ref ** 2
+        assert np.allclose(r["w_hat"], -q / np.linalg.norm(q), atol=1e-8)
+
+
+def test_hmc_step_stays_inside_and_moves_on_the_parabola():
+    n = 3
+    A = W.rotated_cube(n, seed=W.BASE_SEED + 82)
+    c = np.array([1.0, -0.5, 0.3])
+    x = np.zeros(n)
+    for k in range(20):
+        x_new, st, refl = hmc.hmc_step(A, x, c, 1.0, tau=3.0, rho=100, kappa=1e-6, seed=4,
+                                       chain=0, step=k)
+        assert st == 0
+        assert oracle.membership(A, x_new)
+        if refl == 0:
+            # no reflection: the end point is Phi(l) of the step's own draws
+            v = oracle.gaussians(n, 4, 0, k)
+            ell = 3.0 * oracle.uniform(4, 0, k, 1)
+            assert np.allclose(x_new, x + v * ell - c / 2.0 * ell ** 2, atol=1e-14)
+        x = x_new
