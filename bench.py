@@ -59,7 +59,7 @@ def parse():
                         "every path then starts from that state (the same step window)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="learned", choices=["fp64", "mixed", "learned"])
-    p.add_argument("--workload", default="s200", choices=["s200", "batch"],
+    p.add_argument("--workload", default="s200", choices=["s200", "batch", "hmc"],
                    help="s200: the headline (S-200-200, 8192 chains); batch: 64 spectrahedra "
                         "of uneven n, m in one persistent launch")
     p.add_argument("--walk", default="billiard", choices=["billiard", "hnr", "cdhr"],
@@ -604,11 +604,104 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def hmc_workload():
+    """HMC with reflections (Alg. 6) for exp(-c.x / T) on Dabbene S-60-60 (the
+    largest S-n-m of the paper's annealing study, Table 4), c a seeded unit
+    vector, T = 1."""
+    from paper_2010_03817_gb300 import workloads as W
+    A = W.dabbene(60, 60, seed=W.BASE_SEED + 400)
+    g = np.random.default_rng(W.BASE_SEED + 401)
+    c = g.normal(size=60)
+    return A, c / np.linalg.norm(c), 1.0
+
+
+def run_hmc(args):
+    """HMC-r chain-steps/s on one GPU (sp_step_hmc, FP64 curve oracle), the
+    oracle's HMC on a sample of the same chains as the CPU baseline."""
+    import torch
+    from paper_2010_03817_gb300 import build, spectra
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    A, c, T = hmc_workload()
+    n, m = A.shape[0] - 1, A.shape[1]
+    spec = spectra.Spectrahedron(A, fp64_only=True)
+    # tau ~ diam(S): the longest chord through the origin over 256 directions
+    from paper_2010_03817_gb300 import workloads as W
+    D = torch.tensor(W.random_directions(n, 256, seed=W.BASE_SEED + 402), device="cuda")
+    tm, tp, _, _ = spec.intersect(torch.zeros_like(D), D)
+    tau = float((tp - tm).max().item())
+    C = args.chains
+    ch = spectra.Chains(spec, C, seed=SEED_WALK, chain0=rank * C)
+    ch.hmc(args.warmup, c, T, tau, rho=100, kappa=KAPPA)
+    torch.cuda.synchronize()
+    X0, step0 = ch.state_host()
+    _, s0 = ch.status()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        ch.hmc(args.steps, c, T, tau, rho=100, kappa=KAPPA)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    _, s1 = ch.status()
+    segs = s1["segments"] - s0["segments"]
+    value = C * args.steps / (ms / 1e3)
+    P = m * (m + 1) / 2
+    N = 2 * m
+    # per segment: eigenvalues of the 2m companion matrix (Hessenberg + Francis
+    # QR, 10 N^3), two Cholesky factorisations, the triangular solves that
+    # build it (2 m^3), F(p), V, F(Phi(sigma)), F(Phi(t)) and the normal
+    flops_seg = 10.0 * N ** 3 + 2 * m ** 3 / 3 + 2 * m ** 3 + 8 * n * P + 2 * (n + 1) * P
+    achieved = flops_seg * segs / (ms / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        from oracle import hmc as ohmc
+        k, t0, osegs = 0, time.perf_counter(), 0
+        while k < C and (k < 2 or time.perf_counter() - t0 < 20.0):
+            x, st, refl = ohmc.hmc_step(A, X0[k], c, T, tau=tau, rho=100, kappa=KAPPA,
+                                        seed=SEED_WALK, chain=k, step=step0)
+            osegs += refl + 1
+            k += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": k / dt, "unit": "chain-steps/s", "cores": 1, "kind": "oracle",
+               "segments_per_s": osegs / dt,
+               "sample": "chains 0-%d of the warmed-up state, step %d (the GPU's first timed "
+                         "step), oracle/hmc.py (numpy), %.1f s" % (k - 1, step0, dt)}
+    if rank == 0:
+        line = {
+            "metric": "HMC-r Boltzmann chain-steps/s (S-60-60)",
+            "value": value, "unit": "chain-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Dabbene S-60-60 (n=m=60), HMC with reflections for "
+                                   "exp(-c.x/T), c a seeded unit vector, T=1, %d chains" % C,
+                       "tau": tau, "rho": 100, "kappa": KAPPA,
+                       "l2": "per-chain state 8 KB; inputs L2-resident (no flush)"},
+            "oracle_calls_per_s": segs / (ms / 1e3),
+            "segments_per_step": segs / (C * args.steps),
+            "bad_steps": s1["bad_steps"] - s0["bad_steps"],
+            "roofline": {"bound": "alu", "kernel": "curve_kernel", "launches": 1,
+                         "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
+                         "unit": "TFLOP/s (FP64 pipe)", "frac": achieved / PEAK_FP64_TFLOPS,
+                         "peak_source": "derived: 152 SMs x unit count x 2.07 GHz",
+                         "algorithmic_flops_per_segment": flops_seg, "traffic": None},
+            "cpu_baseline": cpu,
+            "gpu_launches": 2,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     global WALK
     args = parse()
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "hmc":
+        return run_hmc(args)
     WALK = args.walk
     if WALK != "billiard" and args.mode == "learned":
         args.mode = "mixed"  # the warm start predicts Billiard segments only

@@ -274,7 +274,7 @@ struct sp_chains {
   int* done = nullptr;
   int* ids[2] = {nullptr, nullptr};
   double* dirs[2] = {nullptr, nullptr};
-  int* counts = nullptr;     // 3: the two wave lists, the F refresh list
+  int* counts = nullptr;     // 4: the two wave lists, the F refresh list, the wave ticket
   int* h_count = nullptr;    // pinned host mirror
   int* fage = nullptr;       // C: updates of each chain's carried F since its formation
   int* ref_ids = nullptr;    // C: chains listed for a fresh formation of F
@@ -844,7 +844,7 @@ static int ensure_chain_mixed(sp_chains* ch) {
             cudaMalloc(&ch->ids[1], sizeof(int) * C) == cudaSuccess &&
             cudaMalloc(&ch->dirs[0], sizeof(double) * (size_t)C * n) == cudaSuccess &&
             cudaMalloc(&ch->dirs[1], sizeof(double) * (size_t)C * n) == cudaSuccess &&
-            cudaMalloc(&ch->counts, 3 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ch->counts, 4 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ch->fage, sizeof(int) * C) == cudaSuccess &&
             cudaMalloc(&ch->ref_ids, sizeof(int) * C) == cudaSuccess &&
             cudaMallocHost(&ch->h_count, sizeof(int)) == cudaSuccess;
@@ -920,6 +920,7 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
   wv.fage = ch->fage;
   wv.ref_ids = ch->ref_ids;
   wv.ref_count = ch->counts + 2;
+  wv.ticket = ch->counts + 3;
   // Billiard: the reflections' normals on the tensor cores, one contraction
   // per wave (deferred from the wave kernel to a finish kernel)
   const bool defer = kind == 0 && s->Bc != nullptr;
@@ -955,6 +956,7 @@ static int run_walk_mixed(sp_chains* ch, int kind, int steps, double tau, int rh
     wv.dir_next = ch->dirs[cur ^ 1];
     wv.count_next = ch->counts + (cur ^ 1);
     e = cudaMemsetAsync(wv.count_next, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wv.ticket, 0, sizeof(int), st);
     if (ch->timing) cudaEventRecord(ev[0], st);
     // V of every listed chain on the tensor cores (CDHR reads V = A_j from
     // the stack instead)

@@ -77,116 +77,206 @@ __device__ __forceinline__ void load4(const T* p, T (&v)[4]) {
   }
 }
 
+// ---- the three steps of one panel (columns jb .. jb + nb) -------------------
+
+// 1. one warp factors the nb x nb diagonal block in registers (lane r holds
+//    row r; column c broadcast by shuffles): L_bb into G, its entries and the
+//    reciprocal pivots into the panel copy pan.  Returns 0 or 1 + the first
+//    bad column (warp-uniform).
+template <typename T, int kPanel>
+__device__ __forceinline__ int chol_diag_block(T* G, int jb, int nb, T* pan, int ld) {
+  const int lane = threadIdx.x & 31;
+  T row[kPanel];
+  const bool mine = lane < nb;
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c)
+    row[c] = (mine && c <= lane) ? G[tri(jb + lane, jb + c)] : T(0);
+  int bad = 0;
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) {
+    if (c < nb && !bad) {
+      const T d = shfl_idx(row[c], c);
+      if (!(d > T(1e-37)) || !(d < T(3e37))) {
+        bad = c + 1;
+      } else {
+        const T rinv = rsqrt_t(d);
+        if (lane == c) row[c] = d * rinv;
+        if (lane > c) row[c] *= rinv;
+#pragma unroll
+        for (int c2 = c + 1; c2 < kPanel; ++c2) {
+          const T l2 = shfl_idx(row[c], c2);
+          if (c2 <= lane) row[c2] -= row[c] * l2;
+        }
+        if (lane == 0) pan[c * ld + jb + c] = rinv;  // 1 / L_cc for step 2
+      }
+    }
+  }
+  if (!bad && mine) {
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c)
+      if (c <= lane) {
+        G[tri(jb + lane, jb + c)] = row[c];
+        if (c < lane) pan[c * ld + jb + lane] = row[c];  // L_bb[lane][c]
+      }
+  }
+  return bad ? jb + bad : 0;
+}
+
+// 2. every row i >= j0 solves against the diagonal block (one thread per
+//    row, forward substitution with the block read as broadcasts from shared
+//    memory) and leaves its entries in the transposed panel copy pan[c][i];
+//    rows m .. ld-1 of the copy are zeroed for the edge tiles of step 3
+template <typename T, int kPanel>
+__device__ __forceinline__ void chol_panel_rows(T* G, int m, int jb, int j0, T* pan, int ld) {
+  const int tid = threadIdx.x;
+  for (int i = j0 + tid; i < m; i += SPG_THREADS) {
+    const size_t base = tri(i, jb);
+    T g[kPanel];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) g[c] = G[base + c];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < c; ++k) mac_acc(acc, g[k], pan[k * ld + jb + c]);
+      g[c] = (g[c] - acc) * pan[c * ld + jb + c];
+    }
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+      G[base + c] = g[c];
+      pan[c * ld + i] = g[c];
+    }
+  }
+  for (int q = tid; q < kPanel * (ld - m); q += SPG_THREADS)
+    pan[(q / (ld - m)) * ld + m + q % (ld - m)] = T(0);
+}
+
+// 3. the rank-kPanel update of the trailing lower triangle (rows and columns
+//    >= j0) in 4 x 4 register tiles (8 + 8 panel loads per 16 kPanel MACs).
+//    Thread `first` of `count` takes every count-th tile, and only rows at or
+//    below `skip` (rows j0 .. skip-1 belong to a block updated elsewhere).
+template <typename T, int kPanel>
+__device__ __forceinline__ void chol_trailing(T* G, int m, int j0, const T* pan, int ld,
+                                              int first, int count, int skip) {
+  const int s = m - j0;
+  const int nt = (s + 3) >> 2;
+  const int ntiles = nt * (nt + 1) / 2;
+  const int I0 = (skip - j0) >> 2;  // tile rows entirely above `skip`
+  for (int t = I0 * (I0 + 1) / 2 + first; t < ntiles; t += count) {
+    int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    const int K = t - I * (I + 1) / 2;
+    const int i0 = j0 + 4 * I, k0 = j0 + 4 * K;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+      T va[4], vb[4];
+      load4<T>(pan + c * ld + i0, va);
+      load4<T>(pan + c * ld + k0, vb);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mac_acc(acc[a][b], va[a], vb[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = i0 + a;
+      if (i < m && i >= skip) {
+        T* gi = G + tri(i, 0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (k0 + b <= i) gi[k0 + b] -= acc[a][b];
+      }
+    }
+  }
+}
+
+// The factorisation described above: steps 1-3 per panel, three barriers.
 template <typename T, int kPanel = spg::kPanel>
 __device__ bool factor_cholesky(T* G, int m, T* pan_raw, int* flag) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, wid = tid >> 5;
   // 16-byte aligned panel base; row stride ld (a multiple of 4, >= m + 3)
   T* pan = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(pan_raw) + 15) & ~uintptr_t(15));
   const int ld = chol_ld(m);
   for (int jb = 0; jb < m; jb += kPanel) {
     const int nb = min(kPanel, m - jb);
     const int j0 = jb + nb;
-    // ---- 1. diagonal block ---------------------------------------------------
     if (wid == 0) {
-      T row[kPanel];
-      const bool mine = lane < nb;
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c)
-        row[c] = (mine && c <= lane) ? G[tri(jb + lane, jb + c)] : T(0);
-      int bad = 0;
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        if (c < nb && !bad) {
-          const T d = shfl_idx(row[c], c);
-          if (!(d > T(1e-37)) || !(d < T(3e37))) {
-            bad = c + 1;
-          } else {
-            const T rinv = rsqrt_t(d);
-            if (lane == c) row[c] = d * rinv;
-            if (lane > c) row[c] *= rinv;
-#pragma unroll
-            for (int c2 = c + 1; c2 < kPanel; ++c2) {
-              const T l2 = shfl_idx(row[c], c2);
-              if (c2 <= lane) row[c2] -= row[c] * l2;
-            }
-            if (lane == 0) pan[c * ld + jb + c] = rinv;  // 1 / L_cc for step 2
-          }
-        }
-      }
-      if (bad) {
-        if (lane == 0) *flag = jb + bad;
-      } else if (mine) {
-#pragma unroll
-        for (int c = 0; c < kPanel; ++c)
-          if (c <= lane) {
-            G[tri(jb + lane, jb + c)] = row[c];
-            if (c < lane) pan[c * ld + jb + lane] = row[c];  // L_bb[lane][c]
-          }
-      }
+      const int bad = chol_diag_block<T, kPanel>(G, jb, nb, pan, ld);
+      if (bad && (tid & 31) == 0) *flag = bad;
     }
     __syncthreads();
     if (*flag) return false;
     if (j0 >= m) break;
-    // ---- 2. panel rows below the block ----------------------------------------
-    for (int i = j0 + tid; i < m; i += SPG_THREADS) {
-      const size_t base = tri(i, jb);
-      T g[kPanel];
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) g[c] = G[base + c];
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < c; ++k) mac_acc(acc, g[k], pan[k * ld + jb + c]);
-        g[c] = (g[c] - acc) * pan[c * ld + jb + c];
-      }
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        G[base + c] = g[c];
-        pan[c * ld + i] = g[c];
-      }
-    }
-    // rows m .. ld-1 of the copy read as zeros by the edge tiles
-    for (int q = tid; q < kPanel * (ld - m); q += SPG_THREADS)
-      pan[(q / (ld - m)) * ld + m + q % (ld - m)] = T(0);
+    chol_panel_rows<T, kPanel>(G, m, jb, j0, pan, ld);
     __syncthreads();
-    // ---- 3. trailing update, 4 x 4 tiles of the lower triangle ---------------
-    const int s = m - j0;
-    const int nt = (s + 3) >> 2;
-    const int ntiles = nt * (nt + 1) / 2;
-    for (int t = tid; t < ntiles; t += SPG_THREADS) {
-      int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-      while (I * (I + 1) / 2 > t) --I;
-      while ((I + 1) * (I + 2) / 2 <= t) ++I;
-      const int K = t - I * (I + 1) / 2;
-      const int i0 = j0 + 4 * I, k0 = j0 + 4 * K;
-      T acc[4][4];
+    chol_trailing<T, kPanel>(G, m, j0, pan, ld, tid, SPG_THREADS, j0);
+    __syncthreads();
+  }
+  return true;
+}
+
+// The same factorisation with a look-ahead of one panel, two barriers per
+// panel: after the panel rows of block b, warp 0 applies block b's update to
+// the next diagonal block itself and factors it, while the other warps apply
+// the update to the rest of the trailing triangle, so the serial chain of
+// the diagonal blocks (a shuffle, a reciprocal square root and a
+// multiply-add per column) overlaps the parallel update instead of stalling
+// the CTA.  Two panel copies alternate (the next block's entries land in one
+// while the other is read).  Every entry receives the same operations in
+// the same order as in factor_cholesky, so the two give identical factors.
+// pan: scratch of cholesky_scratch_la(m, kPanel) elements.
+__host__ __device__ inline size_t cholesky_scratch_la(int m, int pw = kPanel) {
+  return 2 * (size_t)pw * chol_ld(m) + 4;
+}
+template <typename T, int kPanel = spg::kPanel>
+__device__ bool factor_cholesky_la(T* G, int m, T* pan_raw, int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ld = chol_ld(m);
+  T* pans[2];
+  pans[0] = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(pan_raw) + 15) & ~uintptr_t(15));
+  pans[1] = pans[0] + (size_t)kPanel * ld;  // ld is a multiple of 4: still 16-byte aligned
+  if (wid == 0) {
+    const int bad = chol_diag_block<T, kPanel>(G, 0, min(kPanel, m), pans[0], ld);
+    if (bad && lane == 0) *flag = bad;
+  }
+  __syncthreads();
+  if (*flag) return false;
+  for (int jb = 0, p = 0; jb < m; jb += kPanel, p ^= 1) {
+    const int nb = min(kPanel, m - jb);
+    const int j0 = jb + nb;
+    if (j0 >= m) break;
+    T* cur = pans[p];
+    chol_panel_rows<T, kPanel>(G, m, jb, j0, cur, ld);
+    __syncthreads();
+    const int nb2 = min(kPanel, m - j0);
+    const int j1 = j0 + nb2;
+    if (wid == 0) {
+      // block b's update of the next diagonal block (lane r: row j0 + r),
+      // accumulated as the 4 x 4 tiles accumulate it, then its factorisation
+      if (lane < nb2) {
+        const int i = j0 + lane;
+        T* gi = G + tri(i, 0);
+        for (int k = j0; k <= i; ++k) {
+          T acc = T(0);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        T va[4], vb[4];
-        load4<T>(pan + c * ld + i0, va);
-        load4<T>(pan + c * ld + k0, vb);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) mac_acc(acc[a][b], va[a], vb[b]);
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = i0 + a;
-        if (i < m) {
-          T* gi = G + tri(i, 0);
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (k0 + b <= i) gi[k0 + b] -= acc[a][b];
+          for (int c = 0; c < kPanel; ++c) mac_acc(acc, cur[c * ld + i], cur[c * ld + k]);
+          gi[k] -= acc;
         }
       }
+      __syncwarp();
+      const int bad = chol_diag_block<T, kPanel>(G, j0, nb2, pans[p ^ 1], ld);
+      if (bad && lane == 0) *flag = bad;
+    } else {
+      chol_trailing<T, kPanel>(G, m, j0, cur, ld, tid - 32, SPG_THREADS - 32, j1);
     }
     __syncthreads();
+    if (*flag) return false;
   }
   return true;
 }

@@ -16,7 +16,8 @@
 //   Francis double-shift QR for all its eigenvalues (one warp);
 //   the null vector u of F(Phi(t+)) by inverse iteration on F(Phi(sigma)),
 //   sigma just below t+ (a factorisation that succeeds there also certifies
-//   the point interior); t refined on the scalar quadratic u^T F(Phi(t)) u = 0
+//   the point interior), then two corrections toward the null vector of
+//   F(Phi(t)) itself; t refined on the scalar quadratic u^T F(Phi(t)) u = 0
 //   (stationary at u; no root of it lies below t+, since F(Phi(t)) is
 //   positive definite before t+; the refinement is kept within 1e-7 of t);
 //   the normal w_j = u^T A_j u at Phi(t+) (Lemma "Gradient of det F") and the
@@ -411,11 +412,16 @@ __device__ __noinline__ CurveResult curve_segment(const DevSpec& sp, const Curve
   }
   double t = 1.0 / mu;
   // ---- the null vector at the hit point; t refined --------------------------
-  // F(Phi(sigma)) is positive definite for sigma below t+; its smallest
-  // eigenvalue belongs to the null vector of F(Phi(t+)), found by inverse
-  // iteration (gap ratio about (t - sigma) / t per iteration)
+  // F(Phi(sigma)) is positive definite for sigma below t+; inverse iteration
+  // on it gives u0, its eigenvector of the smallest eigenvalue, which is the
+  // null vector of F(Phi(t)) up to O((t - sigma) |F'| / lambda_2).  Two
+  // corrections u <- u - F(Phi(sigma))^{-1} F(Phi(t)) u remove that error:
+  // the iteration's fixed points are the null vectors of F(Phi(t)), and it
+  // contracts the rest by about (t - sigma) |F'| / lambda_2 per step.
   bool ok = false;
+  int used = 0;
   for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+    used = attempt;
     const double sig = t * (1.0 - (attempt == 0 ? 1e-5 : (attempt == 1 ? 1e-3 : 1e-1)));
     for (int j = tid; j < n; j += SPG_THREADS)
       sm.wh[j] = sm.p[j] + sm.v[j] * sig - sm.c[j] / (2.0 * cp.T) * sig * sig;
@@ -431,13 +437,35 @@ __device__ __noinline__ CurveResult curve_segment(const DevSpec& sp, const Curve
   }
   for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = 1.0 + 0.5 * sin(0.9 * i + 0.3);
   __syncthreads();
-  for (int it = 0; it < 4; ++it) {
-    if (wid == 0) warp_llt_solve(sm.L, sm.u, m);
+  // (the corrections only from the closest shift, where they contract)
+  const int iters = used == 0 ? 6 : 4;
+  for (int it = 0; it < iters; ++it) {
+    double* r = sm.hv;
+    if (it >= 4) {
+      // r = F(Phi(t)) u, with F(Phi(t)) formed into the global scratch
+      for (int j = tid; j < n; j += SPG_THREADS)
+        sm.wh[j] = sm.p[j] + sm.v[j] * t - sm.c[j] / (2.0 * cp.T) * t * t;
+      __syncthreads();
+      form_at(sp, sm.wh, Vp);
+      for (int i = tid; i < m; i += SPG_THREADS) {
+        double a = 0.0;
+        for (int k = 0; k < m; ++k) a += Vp[i >= k ? tri(i, k) : tri(k, i)] * sm.u[k];
+        r[i] = a;
+      }
+    } else {
+      for (int i = tid; i < m; i += SPG_THREADS) r[i] = sm.u[i];
+    }
+    __syncthreads();
+    if (wid == 0) warp_llt_solve(sm.L, r, m);
     __syncthreads();
     double a = 0.0;
-    for (int i = tid; i < m; i += SPG_THREADS) a += sm.u[i] * sm.u[i];
-    const double r = 1.0 / sqrt(block_sum(a, sm.red));
-    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] *= r;
+    for (int i = tid; i < m; i += SPG_THREADS) {
+      const double ui = it >= 4 ? sm.u[i] - r[i] : r[i];
+      sm.u[i] = ui;
+      a += ui * ui;
+    }
+    const double rn = 1.0 / sqrt(block_sum(a, sm.red));
+    for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] *= rn;
     __syncthreads();
   }
   // w_j = u^T A_j u, j = 0..n (packed: off-diagonal entries twice)
@@ -654,6 +682,11 @@ int curve_setup(const spg::DevSpec& sp, const double* c, double T, cudaStream_t 
                 double** Cp, const char* too_big) {
   *dc = *Cp = nullptr;
   if (sp.m > spg::kCurveMaxM) return spg_set_error(SP_EINVAL, too_big);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (spg::curve_smem_bytes(sp.n, sp.m) > (size_t)optin)
+    return spg_set_error(SP_EINVAL, "curve: n too large for the shared-memory layout");
   if (cudaMallocAsync(dc, sizeof(double) * sp.n, st) != cudaSuccess ||
       cudaMallocAsync(Cp, sizeof(double) * sp.P, st) != cudaSuccess) {
     cudaGetLastError();

@@ -182,6 +182,7 @@ struct MixWave {
   int* fage;        // C updates since the last fresh formation
   int* ref_ids;     // chains listed for the next wave's formation of F
   int* ref_count;
+  int* ticket;  // the wave's line counter (zero at launch): lines are taken in order, one per CTA at a time
 };
 // updates of a carried F between fresh formations: Billiard and Hit-and-Run,
 // CDHR (whose update F + t A_j the paper prescribes)

@@ -27,8 +27,7 @@
 namespace spg {
 namespace {
 
-constexpr int kStage2Panel = 16;  // panel width of the double-float factorisation
-static_assert(kStage2Panel <= kMaxPanel, "the panel scratch holds up to kMaxPanel columns");
+constexpr int kStage2Panel = 8;  // panel width of the double-float factorisation
 
 struct MixSmem {
   uint8_t* R;     // region: stage 1 (G32, V32), stage 2 (G64), stage 3 (U hi, lo)
@@ -41,7 +40,7 @@ struct MixSmem {
   double* z;      // m
   double* u;      // m
   double* um;     // m (null vector at t-)
-  double* part;   // SPG_WARPS * m + 64
+  double* part;   // SPG_WARPS * m + 128 (>= cholesky_scratch_la(m, 8) for any m)
   double* scr;    // SPG_SCR
   double* bc;     // 16
   float* q32;     // m
@@ -80,7 +79,7 @@ __device__ MixSmem mix_carve(uint8_t* base, int n, int m, uint8_t* region_global
   s.z = d; d += m;
   s.u = d; d += m;
   s.um = d; d += m;
-  s.part = d; d += (size_t)SPG_WARPS * m + 128;  // also the Cholesky panel (up to 16 wide)
+  s.part = d; d += (size_t)SPG_WARPS * m + 128;  // also the two look-ahead panel copies
   s.scr = d; d += SPG_SCR;
   s.bc = d; d += 16;
   float* f = reinterpret_cast<float*>(d);
@@ -268,6 +267,15 @@ __device__ __noinline__ double pencil_rq(const double* Fg, const double* Vg, con
   return -df_to_double(ah, al) / df_to_double(bh, bl);
 }
 
+// the two look-ahead factorisations, not inlined: each gets the full
+// register budget instead of sharing it with its caller's live values
+__device__ __noinline__ bool factor_df_la(dfloat* G, int m, dfloat* pan, int* flag) {
+  return factor_cholesky_la<dfloat, kStage2Panel>(G, m, pan, flag);
+}
+__device__ __noinline__ bool factor_f32_la(float* G, int m, float* pan, int* flag) {
+  return factor_cholesky_la<float>(G, m, pan, flag);
+}
+
 // Stage 2 in double-float for one end of the chord (the FP32 pipe; on this
 // GPU the FP64 pipe runs at about 1/58 of its rate).  The factorisation next
 // to the boundary needs more than FP32: F + sigma1 V is within delta of
@@ -310,9 +318,8 @@ __device__ __noinline__ int refine_end_dd(const DevSpec& sp, const MixWork& mw, 
     }
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
-    // 16-column panels: half the barrier rounds of the default width for the
-    // factorisation that dominates the segment
-    ok = factor_cholesky<T, kStage2Panel>(G, m, part, &sm.ib[0]);
+    // the factorisation that dominates the segment: look-ahead of one panel
+    ok = factor_df_la(G, m, part, &sm.ib[0]);
     if (!ok) {
       ++res->retries;
       delta *= 8.0;
@@ -615,7 +622,7 @@ __device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork
       }
       if (tid == 0) sm.ib[0] = 0;
       __syncthreads();
-      okl = factor_cholesky<float>(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
+      okl = factor_f32_la(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
       if (!okl) ++res.retries;
     }
     stage_mark(mw, 0, tmark);
@@ -653,7 +660,7 @@ __device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork
     }
     if (tid == 0) sm.ib[0] = 0;
     __syncthreads();
-    ok = factor_cholesky<float>(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
+    ok = factor_f32_la(G32, m, reinterpret_cast<float*>(sm.part), &sm.ib[0]);
     if (!ok) {
       ++res.retries;
       sigma0 *= 0.2;  // back off toward the point itself
@@ -947,7 +954,15 @@ __global__ void __launch_bounds__(SPG_THREADS, 1)
   float* Q32 = mw.Q32 + cta * (size_t)mw.kmax32 * m;
   double* Q64 = mw.Q64 + cta * (size_t)mw.kmax64 * m;
   const int count = *wv.count_cur;
-  for (int r = blockIdx.x; r < count; r += gridDim.x) {
+  for (;;) {
+    // the next line from the wave's counter: a CTA that drew expensive lines
+    // (long eigen-solves, FP64 fallbacks) takes fewer, so the wave ends
+    // within about one segment of its mean load
+    if (tid == 0) sm.ib[5] = atomicAdd(wv.ticket, 1);
+    __syncthreads();
+    const int r = sm.ib[5];
+    __syncthreads();
+    if (r >= count) break;
     const int c = wv.id_cur[r];
     double* Fc = wv.F + (size_t)c * P;
     for (int j = tid; j < n; j += SPG_THREADS) {

@@ -29,6 +29,24 @@ def load_example_2d():
     return np.array(mats, dtype=np.float64)
 
 
+def boltzmann_moments_2d(A, c, T, half=7.0, k=561):
+    """E[x] and Var[x] of exp(-c.x / T) restricted to the 2D spectrahedron,
+    by the midpoint rule on a k x k grid over [-half, half]^2 (membership by
+    numpy's eigenvalues of F(x); the body must not touch the grid's border)."""
+    h = 2 * half / k
+    g = -half + h * (np.arange(k) + 0.5)
+    X1, X2 = np.meshgrid(g, g, indexing="ij")
+    F = A[0][None, None] + X1[..., None, None] * A[1] + X2[..., None, None] * A[2]
+    inside = np.linalg.eigvalsh(F)[..., 0] > 0
+    assert not inside[0].any() and not inside[-1].any()
+    assert not inside[:, 0].any() and not inside[:, -1].any()
+    wgt = np.where(inside, np.exp(-(c[0] * X1 + c[1] * X2) / T), 0.0)
+    Z = wgt.sum()
+    mean = np.array([(wgt * X1).sum(), (wgt * X2).sum()]) / Z
+    var = np.array([(wgt * X1 ** 2).sum(), (wgt * X2 ** 2).sum()]) / Z - mean ** 2
+    return mean, var, inside.sum() * h * h
+
+
 @pytest.fixture(scope="session")
 def example_2d():
     return load_example_2d()

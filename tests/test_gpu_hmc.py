@@ -182,3 +182,22 @@ def test_boltzmann_cube_marginals(S):
             var = 1.0 / lam ** 2 - 1.0 / math.sinh(lam) ** 2
         se = math.sqrt(var / C)
         assert abs(X[:, i].mean() - mean) <= 5 * se, (i, X[:, i].mean(), mean, se)
+
+
+def test_fig4_boltzmann_means(S, example_2d):
+    """Fig. 4 (right): T = 1, c = (-0.09, 1) on the Appendix B spectrahedron;
+    4096 GPU chains from (-1, 1) reproduce the density's mean (quadrature)
+    within five standard errors."""
+    import conftest
+    A = example_2d
+    c, T = np.array([-0.09, 1.0]), 1.0
+    mean, var, _ = conftest.boltzmann_moments_2d(A, c, T)
+    spec = S.Spectrahedron(A)
+    C = 4096
+    ch = S.Chains(spec, C, x0=np.tile([-1.0, 1.0], (C, 1)), seed=23)
+    ch.hmc(25, c, T, tau=6.0, rho=100, kappa=1e-6)
+    X, _ = ch.state_host()
+    _, stats = ch.status()
+    assert stats["bad_steps"] == 0 and stats["reflections"] > 0
+    se = np.sqrt(var / C)
+    assert np.all(np.abs(X.mean(axis=0) - mean) <= 5 * se), (X.mean(axis=0), mean, se)

@@ -14,6 +14,7 @@ Boltzmann density) against what the geometry fixes without it:
 import numpy as np
 import pytest
 
+import conftest
 import oracle
 from oracle import hmc
 from paper_2010_03817_gb300 import workloads as W
@@ -104,3 +105,28 @@ def test_hmc_step_stays_inside_and_moves_on_the_parabola():
             ell = 3.0 * oracle.uniform(4, 0, k, 1)
             assert np.allclose(x_new, x + v * ell - c / 2.0 * ell ** 2, atol=1e-14)
         x = x_new
+
+
+def test_fig4_boltzmann_means(example_2d):
+    """Fig. 4 (right): the Boltzmann density with T = 1, c = (-0.09, 1) on the
+    Appendix B spectrahedron.  The oracle's HMC chains (Alg. 6) reproduce the
+    density's mean, computed here by quadrature, within five standard errors
+    of their independent end points."""
+    A = example_2d
+    c, T = np.array([-0.09, 1.0]), 1.0
+    mean, var, area = conftest.boltzmann_moments_2d(A, c, T)
+    assert abs(area - 10.45) < 0.1  # the area of the reading C1 (Sec. 2.5 example)
+    chains, steps = 300, 12
+    ends = []
+    for ch in range(chains):
+        x = np.array([-1.0, 1.0])
+        for k in range(steps):
+            x, st, _ = hmc.hmc_step(A, x, c, T, tau=6.0, rho=100, kappa=1e-6, seed=21,
+                                    chain=ch, step=k)
+            assert st == 0
+        ends.append(x)
+    ends = np.array(ends)
+    se = np.sqrt(var / chains)
+    assert np.all(np.abs(ends.mean(axis=0) - mean) <= 5 * se), (ends.mean(axis=0), mean, se)
+    # the density is not the uniform one: its second moment is pulled down
+    assert mean[1] < -0.3
