@@ -305,11 +305,13 @@ def alg_flops_fp64_contraction(n, m, segments):
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PROBE_FP32_TFLOPS, PROBE_FP64_TFLOPS = 69.8, 1.19
-# dram__bytes_read.sum + dram__bytes_write.sum of mixed_wave_kernel per
-# segment (ncu, one wave of 152 lines of this workload; the carried F and V
-# read, F written); None once the kernel changes until the next capture
-WAVE_DRAM_BYTES_PER_SEGMENT = None
-FP64_DRAM_BYTES_PER_SEGMENT = None
+# dram__bytes_read.sum + dram__bytes_write.sum per segment from one ncu
+# capture of the current kernels (profiles/): mixed_wave_kernel on one wave
+# of 152 single-segment lines of this workload (74.45 + 49.54 MB), and
+# walk_fp64_kernel on one step of 152 chains (149.90 + 137.19 MB); None once
+# a kernel changes until the next capture
+WAVE_DRAM_BYTES_PER_SEGMENT = (74.454016e6 + 49.536256e6) / 152
+FP64_DRAM_BYTES_PER_SEGMENT = (149.895168e6 + 137.188608e6) / 152
 
 
 def _peaks():
