@@ -331,26 +331,46 @@ struct CurveResult {
 
 // The boundary oracle of the trajectory Phi(t) = p + v t - (c/(2T)) t^2
 // (sm.p, sm.v, sm.c).  On kOk: t_plus, the unit normal in sm.wh.
+// sigma0 >= 0: the expansion point (below; 0 at a step start).
 __device__ __noinline__ CurveResult curve_segment(const DevSpec& sp, const CurveParams& cp,
-                                                  CurveSmem& sm, double* __restrict__ Vp) {
+                                                  CurveSmem& sm, double* __restrict__ Vp,
+                                                  double sigma0) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = sp.n, m = sp.m, N = 2 * m, ld = curve_ld(m);
   const long long P = sp.P;
   CurveResult res;
   res.t_plus = 0.0;
-  // ---- F(p) and V; Cholesky of F --------------------------------------------
-  form_at(sp, sm.p, sm.L);
-  for (long long e = tid; e < P; e += SPG_THREADS) {
-    const double* Ae = sp.A + e;
-    double g = 0.0;
-    for (int j = 0; j < n; ++j) g += sm.v[j] * Ae[(size_t)(j + 1) * P];
-    Vp[e] = g;
-  }
-  if (tid == 0) sm.ib[0] = 0;
-  __syncthreads();
-  if (!factor_cholesky<double>(sm.L, m, sm.col, &sm.ib[0])) {
-    res.status = kNotPD;
-    return res;
+  // ---- the pencil at the expansion point s0 ---------------------------------
+  // After a reflection the walker sits kappa-close to the boundary it left:
+  // F(p) is then nearly singular, L^{-1} huge and the companion matrix badly
+  // scaled (its Francis iteration converges slowly or not at all).  As the
+  // line walks do, the expansion moves a little along the curve:
+  // F(Phi(s0 + s)) = F(Phi(s0)) + s (V + 2 s0 C) + s^2 C, the same quadratic
+  // eigenvalue problem from the point Phi(s0) with velocity Phi'(s0); its
+  // roots s give t = s0 + s (the boundary left behind: t < 0).  s0 backs off
+  // x0.2 (then 0) while F(Phi(s0)) does not factor.
+  double s0 = sigma0 > 0.0 ? sigma0 : 0.0;
+  for (int attempt = 0;; ++attempt) {
+    for (int j = tid; j < n; j += SPG_THREADS) {
+      sm.wh[j] = sm.p[j] + sm.v[j] * s0 - sm.c[j] / (2.0 * cp.T) * s0 * s0;
+      sm.w[j] = sm.v[j] - sm.c[j] / cp.T * s0;
+    }
+    __syncthreads();
+    form_at(sp, sm.wh, sm.L);
+    for (long long e = tid; e < P; e += SPG_THREADS) {
+      const double* Ae = sp.A + e;
+      double g = 0.0;
+      for (int j = 0; j < n; ++j) g += sm.w[j] * Ae[(size_t)(j + 1) * P];
+      Vp[e] = g;
+    }
+    if (tid == 0) sm.ib[0] = 0;
+    __syncthreads();
+    if (factor_cholesky<double>(sm.L, m, sm.col, &sm.ib[0])) break;
+    if (s0 == 0.0) {
+      res.status = kNotPD;
+      return res;
+    }
+    s0 = attempt < 2 ? 0.2 * s0 : 0.0;
   }
   // ---- the companion G = [[0, I], [-K, -B]] ---------------------------------
   // S -> L^{-1} S (columns, in the upper-right block), its transpose into the
@@ -397,20 +417,25 @@ __device__ __noinline__ CurveResult curve_segment(const DevSpec& sp, const Curve
     return res;
   }
   if (tid == 0) {
-    double mu = 0.0;
-    for (int i = 0; i < N; ++i)
-      if (sm.wr[i] > 0.0 && fabs(sm.wi[i]) <= 1e-10 * fabs(sm.wr[i]) && sm.wr[i] > mu)
-        mu = sm.wr[i];
-    sm.bc[0] = mu;
+    // the first root ahead: the smallest t = s0 + 1/mu > 0 over the real
+    // eigenvalues (mu = 0: a root at infinity)
+    double best = INFINITY;
+    for (int i = 0; i < N; ++i) {
+      const double mu = sm.wr[i];
+      if (mu != 0.0 && fabs(sm.wi[i]) <= 1e-10 * fabs(mu)) {
+        const double tk = s0 + 1.0 / mu;
+        if (tk > 0.0 && tk < best) best = tk;
+      }
+    }
+    sm.bc[0] = best;
   }
   __syncthreads();
-  const double mu = sm.bc[0];
-  if (!(mu > 0.0)) {
+  double t = sm.bc[0];
+  if (!(t < INFINITY)) {
     res.status = kUnbounded;
     res.t_plus = INFINITY;
     return res;
   }
-  double t = 1.0 / mu;
   // ---- the null vector at the hit point; t refined --------------------------
   // F(Phi(sigma)) is positive definite for sigma below t+; inverse iteration
   // on it gives u0, its eigenvector of the smallest eigenvalue, which is the
@@ -545,7 +570,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1) curve_kernel(DevSpec sp, Curve
         sm.v[j] = cp.v[(size_t)item * n + j];
       }
       __syncthreads();
-      const CurveResult r = curve_segment(sp, cp, sm, Vp);
+      const CurveResult r = curve_segment(sp, cp, sm, Vp, 0.0);
       if (r.status == kOk) {
         const double vw = velocity_dot_normal(sm, n, cp.T, r.t_plus);
         for (int j = tid; j < n; j += SPG_THREADS) {
@@ -586,8 +611,9 @@ __global__ void __launch_bounds__(SPG_THREADS, 1) curve_kernel(DevSpec sp, Curve
       double ell = cp.tau * rng_uniform(cp.seed, chain, step, kStreamEta);
       __syncthreads();
       int refl = 0, status = kOk;
+      double tprev = 0.0;  // the last hit's t+ within this step (0 at its start)
       for (;;) {
-        const CurveResult r = curve_segment(sp, cp, sm, Vp);
+        const CurveResult r = curve_segment(sp, cp, sm, Vp, 0.1 * tprev);
         ++segs;
         if (r.status != kOk) {
           status = r.status;
@@ -604,6 +630,7 @@ __global__ void __launch_bounds__(SPG_THREADS, 1) curve_kernel(DevSpec sp, Curve
           }
           __syncthreads();
           ell -= tp;
+          tprev = tp;
           if (++refl > cp.rho) {
             status = kRho;
             break;
