@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--delta1", type=float, default=None,
                    help="stage-2 shift of the mixed paths, sigma1 = sigma0 + (t~ - sigma0)(1 - "
                         "delta1) (library default 2e-4)")
+    p.add_argument("--dump-checked", default=None,
+                   help="save the checked calls and their errors to PREFIX_<path>.npz")
     p.add_argument("--check-samples", type=int, default=384,
                    help="boundary-oracle calls of each timed walk checked against the oracle")
     p.add_argument("--train-tuples", type=int, default=262144)
@@ -306,11 +308,11 @@ PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PROBE_FP32_TFLOPS, PROBE_FP64_TFLOPS = 69.8, 1.19
 # dram__bytes_read.sum + dram__bytes_write.sum per segment from one ncu
-# capture of the current kernels (profiles/): mixed_wave_kernel on one wave
-# of 152 single-segment lines of this workload (74.45 + 49.54 MB), and
-# walk_fp64_kernel on one step of 152 chains (149.90 + 137.19 MB); None once
-# a kernel changes until the next capture
-WAVE_DRAM_BYTES_PER_SEGMENT = (74.454016e6 + 49.536256e6) / 152
+# capture of the current kernels (profiles/): walk_fp64_kernel on one step
+# of 152 chains (149.90 + 137.19 MB); mixed_wave_kernel (816 KB per segment
+# on one wave of 152 single-segment lines) has changed since its capture;
+# None once a kernel changes until the next capture
+WAVE_DRAM_BYTES_PER_SEGMENT = None  # changed since its capture (the correction's sum)
 FP64_DRAM_BYTES_PER_SEGMENT = (149.895168e6 + 137.188608e6) / 152
 
 
@@ -432,7 +434,7 @@ def time_path(spectra, torch, spec, mode, C, rank, steps, warmup, tau, flush, st
                 steps=steps, warm_state=warm_state, segments=seg)
 
 
-def oracle_check(A, seg, tol):
+def oracle_check(A, seg, tol, dump=None):
     """t+ and the unit normal of the timed walk's own recorded boundary-oracle
     calls (sp_record_segments, sampled over the whole timed window) against
     the FP64 oracle on the same lines.  The normal is compared for segments
@@ -467,6 +469,13 @@ def oracle_check(A, seg, tol):
         em = np.zeros(0)
     out["pass"] = bool(len(et) >= 256 and et.max() <= tol and
                        (len(ew) == 0 or ew.max() <= tol) and (len(em) == 0 or em.max() <= tol))
+    if dump:
+        # every checked call with its error and the solver-path flags, for
+        # looking at the worst ones against the oracle
+        np.savez(dump, p=P[good], v=V[good], t_gpu=seg["t_plus"][ok][good],
+                 t_oracle=ref["t_plus"][good], err=et, flags=seg["flags"][ok][good],
+                 chain=seg["chain"][ok][good], step=seg["step"][ok][good],
+                 k=seg["k"][ok][good], rel_gap=ref["rel_gap"][good])
     return out
 
 
@@ -866,8 +875,10 @@ def main():
             oracle.build()
             for mode, r in list(context.items()) + [(args.mode, head)]:
                 if r["segments"] is not None:
-                    checks[mode] = oracle_check(A, r["segments"],
-                                                1e-10 if mode == "fp64" else 1e-9)
+                    checks[mode] = oracle_check(
+                        A, r["segments"], 1e-10 if mode == "fp64" else 1e-9,
+                        dump=(args.dump_checked + "_" + mode + ".npz") if args.dump_checked
+                        else None)
 
         except Exception as exc:
             checks = {"failed": str(exc)}

@@ -539,12 +539,24 @@ __device__ __forceinline__ double block_sum_dd(double s, double c, double* red) 
   return s + c;
 }
 
+// Pencil Rayleigh correction of a root t0 of det(F + tV) with null-vector
+// estimate u (CTA-wide, FP64), in the two forms below:
+//   t = t0 - u^T (F + t0 V) u / (u^T V u),
+// the Newton step of the Rayleigh quotient t(u) = -(u^T F u)/(u^T V u),
+// which is stationary at the null vector: its error is quadratic in the
+// error of u, and it is evaluated on the exact FP64 F and V instead of
+// through a factorisation, so the factorisation's backward error (about
+// m eps |F|, large when |F| >> |u^T F u|) does not enter t.  F: packed
+// lower triangle (global or shared); V: packed (vfull = false) or full
+// m x m row-major (vfull = true); pidx: (i << 16) | k per packed entry; u:
+// shared, m.  Both return NaN if u^T V u == 0.
+//
 // The pencil Rayleigh correction of the FP64 path, with F(p) = A_0 + Y kept
 // in two parts (Y = sum_{j>=1} p_j A_j): the large and exact A_0 part of
 //   u^T (F + t0 V) u = u^T A_0 u + u^T (Y + t0 V) u
 // is summed with error-free products and sums (Ogita, Rump, Oishi 2005,
 // Dot2), so that neither the rounding of A_0 + Y nor that of the sum enters
-// t; the small part in plain FP64.  Arguments as pencil_correct; A0 packed
+// t; the small part in plain FP64.  Arguments as above (F = A0 + Y); A0 packed
 // (global); red: 2 SPG_WARPS doubles.
 __device__ inline double pencil_correct_split(const double* __restrict__ A0,
                                               const double* __restrict__ Y,
@@ -576,33 +588,44 @@ __device__ inline double pencil_correct_split(const double* __restrict__ A0,
   return b != 0.0 ? t0 - num / b : NAN;
 }
 
-// Pencil Rayleigh correction of a root t0 of det(F + tV) with null-vector
-// estimate u (CTA-wide, FP64):
-//   t = t0 - u^T (F + t0 V) u / (u^T V u),
-// the Newton step of the Rayleigh quotient t(u) = -(u^T F u)/(u^T V u),
-// which is stationary at the null vector: its error is quadratic in the
-// error of u, and it is evaluated on the exact FP64 F and V instead of
-// through a factorisation, so the factorisation's backward error (about
-// m eps |F|, large when |F| >> |u^T F u|) does not enter t.  F: packed
-// lower triangle (global or shared); V: packed (vfull = false) or full
-// m x m row-major (vfull = true); pidx: (i << 16) | k per packed entry; u:
-// shared, m; red: SPG_WARPS doubles.  Returns NaN if u^T V u == 0.
-__device__ inline double pencil_correct(const double* __restrict__ F, const double* __restrict__ V,
-                                        bool vfull, int m, long long P,
-                                        const uint32_t* __restrict__ pidx, const double* u,
-                                        double t0, double* red) {
-  double a = 0.0, b = 0.0;
+// The pencil Rayleigh correction for an F with large entries and no A_0 + Y
+// split (the mixed path's carried F): u^T (F + t0 V) u is summed with
+// error-free transformations throughout (Dot2, Ogita, Rump, Oishi 2005):
+// x = F + t0 V as an exact pair (TwoProduct of t0 V, TwoSum with F), the
+// products x U_e exact, the running sum a TwoSum pair.  Plain FP64 summation
+// of terms of size |F| |u|^2 (their magnitudes add up to about |F|, 10^3-10^4
+// for the S-n-m bodies) leaves an error of about 10^-14 in a sum whose value
+// is 0 at the root, which short chords at grazing incidence divide by
+// t |u^T V u| ~ 10^-5.  Arguments as above (V packed); red:
+// 2 SPG_WARPS doubles.
+__device__ inline double pencil_correct_dot2(const double* __restrict__ F,
+                                             const double* __restrict__ V, int m, long long P,
+                                             const uint32_t* __restrict__ pidx, const double* u,
+                                             double t0, double* red) {
+  (void)m;
+  double s = 0.0, c = 0.0, b = 0.0;
   for (long long e = threadIdx.x; e < P; e += SPG_THREADS) {
     const uint32_t ik = pidx[e];
     const int i = ik >> 16, k = ik & 0xffff;
-    const double ve = vfull ? V[(size_t)i * m + k] : V[e];
-    const double uu = (i == k ? 1.0 : 2.0) * (u[i] * u[k]);
-    a = fma(fma(t0, ve, F[e]), uu, a);
-    b = fma(ve, uu, b);
+    const double ve = V[e];
+    const double f = i == k ? 1.0 : 2.0;
+    const double uh = f * (u[i] * u[k]);
+    const double ul = f * fma(u[i], u[k], -(u[i] * u[k]));
+    const double tv = t0 * ve;
+    const double tvl = fma(t0, ve, -tv);
+    double x, xl;
+    two_sum64(F[e], tv, x, xl);
+    xl += tvl;
+    const double ph = x * uh;
+    const double pl = fma(x, uh, -ph) + (x * ul + xl * uh);
+    double es;
+    two_sum64(s, ph, s, es);
+    c += es + pl;
+    b = fma(ve, uh, b);
   }
-  a = block_sum(a, red);
+  const double num = block_sum_dd(s, c, red);
   b = block_sum(b, red);
-  return b != 0.0 ? t0 - a / b : NAN;
+  return b != 0.0 ? t0 - num / b : NAN;
 }
 
 }  // namespace spg

@@ -561,11 +561,12 @@ __device__ __noinline__ int refine_end(const DevSpec& sp, const MixWork& mw, Mix
     }
   }
   if (st == kOk) {
-    // the pencil Rayleigh correction on the exact F and V: removes the
-    // factorisation's backward error (about m eps |F|) from t.  The quotient
-    // never lies below the root (F + t+ V is semidefinite), so a correction
-    // is kept only within 1e-7 of t, well inside the walk's backoff kappa.
-    const double tr = pencil_correct(Fg, Vg, false, sp.m, sp.P, sp.pidx, sm.u, *t, sm.sc->red);
+    // the pencil Rayleigh correction on the exact F and V, summed without
+    // rounding error: removes the factorisation's backward error (about
+    // m eps |F|) from t.  The quotient never lies below the root (F + t+ V is
+    // semidefinite), so a correction is kept only within 1e-7 of t, well
+    // inside the walk's backoff kappa.
+    const double tr = pencil_correct_dot2(Fg, Vg, sp.m, sp.P, sp.pidx, sm.u, *t, sm.scr);
     if ((plus ? tr > 0.0 : tr < 0.0) && fabs(tr - *t) <= 1e-7 * fabs(*t)) *t = tr;
   }
   return st;
