@@ -513,7 +513,7 @@ def train_network(spectra, torch, spec, X, Y, cnt, epochs, record_s, walk_steps)
 
 
 def batch_workload():
-    """Config 3 of the build: 64 spectrahedra ball block (r = 3) + random block
+    """The uneven batch: 64 spectrahedra ball block (r = 3) + random block
     with n, k = round(log-uniform[20, 200]) (seeded), 10,000 chains split in
     proportion to n (the remainder to the largest n)."""
     from paper_2010_03817_gb300 import workloads as W
