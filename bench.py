@@ -194,16 +194,16 @@ def cpu_oracle_rate(A, tau, X, step0, chains=32, steps=1):
 
 def run_reference(args):
     """The oracle (FP64, Cholesky + Jacobi, OpenMP over chains) on the GPU
-    arms' workload and step window: chains 0..31 from the same start cloud
+    arms' workload and step window: chains 0..15 from the same start cloud
     walk the same burn-in and warm-up steps (untimed), then the --steps timed
-    steps, each a bounded sample of the bench step (32 of the 8192 chains)."""
+    steps, each a bounded sample of the bench step (16 of the 8192 chains)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
     A = workload()
-    chains = 32  # two chains per host core of the box
+    chains = 16  # one chain per host core of the box: 20 steps end in about 3 minutes
     X = start_points(CHAINS, 0)[:chains]
     X, _ = oracle.walk("billiard", A, X, args.burn_in + args.warmup, tau=TAU, rho=RHO,
                        kappa=KAPPA, seed=SEED_WALK, step0=0, chain0=0)
