@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -59,14 +60,16 @@ def parse():
                         "every path then starts from that state (the same step window)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="learned", choices=["fp64", "mixed", "learned"])
-    p.add_argument("--workload", default="s200", choices=["s200", "batch", "hmc"],
+    p.add_argument("--workload", default="s200",
+                   choices=["s200", "batch", "hmc", "ball10", "ball40", "cube40"],
                    help="s200: the headline (S-200-200, 8192 chains); batch: 64 spectrahedra "
                         "of uneven n, m in one persistent launch")
     p.add_argument("--walk", default="billiard", choices=["billiard", "hnr", "cdhr"],
                    help="the walk timed (the headline is the Billiard walk; Hit-and-Run and "
                         "CDHR are context lines: CDHR reads V = A_j instead of forming it)")
     p.add_argument("--only", action="store_true", help="time the --mode path alone")
-    p.add_argument("--chains", type=int, default=CHAINS)
+    p.add_argument("--chains", type=int, default=None,
+                   help="chains per GPU (default: the workload's, 8192 for S-200-200)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-check", action="store_true", help="skip the sampled oracle check")
@@ -90,9 +93,42 @@ def parse():
     return p.parse_args()
 
 
+# The smaller bodies of the same walk (every path, same flow and checks):
+# name -> (body, n, m, chains, tau = diam(S), description)
+def _sized_workloads():
+    from paper_2010_03817_gb300 import workloads as W
+    return {
+        "ball10": (lambda: W.ball_random(10, 10, 3.0, seed=W.BASE_SEED + 500), 10, 21, 64, 6.0,
+                   "ball block r=3 + random block k=10 (n=10, m=21), 64 chains, Billiard walk"),
+        "ball40": (lambda: W.ball_random(40, 40, 3.0, seed=W.BASE_SEED + 501), 40, 81, 4096, 6.0,
+                   "ball block r=3 + random block k=40 (n=40, m=81), 4096 chains, Billiard walk"),
+        "cube40": (lambda: W.rotated_cube(40, seed=W.BASE_SEED + 502), 40, 80, 4096,
+                   2.0 * math.sqrt(40.0),
+                   "rotated cube [-1,1]^40 (n=40, m=80), 4096 chains, Billiard walk"),
+    }
+
+
+_BODY = None
+
+
 def workload():
     from paper_2010_03817_gb300 import workloads as W
+    if _BODY is not None:
+        return _BODY()
     return W.dabbene(N_DIM, M_DIM, seed=SEED_SPEC)
+
+
+def metric_name(walk):
+    if _BODY is None:
+        return "%s steps/s at n=m=200" % walk
+    return "%s steps/s at n=%d, m=%d" % (walk, N_DIM, M_DIM)
+
+
+def use_workload(name):
+    """Switch the module's workload constants to one of the smaller bodies."""
+    global N_DIM, M_DIM, CHAINS, TAU, WORKLOAD, _BODY
+    body, n, m, chains, tau, desc = _sized_workloads()[name]
+    N_DIM, M_DIM, CHAINS, TAU, WORKLOAD, _BODY = n, m, chains, tau, desc, body
 
 
 def replica_plan(rank, world, C):
@@ -219,7 +255,7 @@ def run_reference(args):
     total = sum(times)
     value = chains * args.steps / total
     line = {
-        "impl": "reference", "metric": "billiard steps/s at n=m=200", "value": value,
+        "impl": "reference", "metric": metric_name("billiard"), "value": value,
         "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -643,7 +679,7 @@ def run_hmc(args):
     D = torch.tensor(W.random_directions(n, 256, seed=W.BASE_SEED + 402), device="cuda")
     tm, tp, _, _ = spec.intersect(torch.zeros_like(D), D)
     tau = float((tp - tm).max().item())
-    C = args.chains
+    C = args.chains or 8192
     ch = spectra.Chains(spec, C, seed=SEED_WALK, chain0=rank * C)
     ch.hmc(args.warmup, c, T, tau, rho=100, kappa=KAPPA)
     torch.cuda.synchronize()
@@ -713,6 +749,10 @@ def main():
         return run_batch(args)
     if args.workload == "hmc":
         return run_hmc(args)
+    if args.workload in ("ball10", "ball40", "cube40"):
+        use_workload(args.workload)
+    if args.chains is None:
+        args.chains = CHAINS
     WALK = args.walk
     if WALK != "billiard" and args.mode == "learned":
         args.mode = "mixed"  # the warm start predicts Billiard segments only
@@ -920,7 +960,7 @@ def main():
                        + kt["mlp_launches"] + kt["other_launches"] + kt["contract_launches"]
                        + kt["finish_launches"])
         line = {
-            "metric": "%s steps/s at n=m=200" % WALK,
+            "metric": metric_name(WALK),
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
