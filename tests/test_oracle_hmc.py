@@ -130,3 +130,49 @@ def test_fig4_boltzmann_means(example_2d):
     assert np.all(np.abs(ends.mean(axis=0) - mean) <= 5 * se), (ends.mean(axis=0), mean, se)
     # the density is not the uniform one: its second moment is pulled down
     assert mean[1] < -0.3
+
+
+def test_reflection_keeps_the_speed():
+    """Reflection on the normal is an isometry: |s| = |Phi'(t+)|, and the
+    normal component changes sign (Sec. 2.4)."""
+    A = W.ball_random(6, 5, 2.0, seed=W.BASE_SEED + 83)
+    g = np.random.default_rng(7)
+    for _ in range(5):
+        p = g.uniform(-0.2, 0.2, 6)
+        v = g.normal(size=6)
+        c = g.normal(size=6)
+        r = hmc.curve_reflect(A, p, v, c, 0.8)
+        assert r["status"] == 0
+        vel = v - c / 0.8 * r["t_plus"]
+        assert abs(np.linalg.norm(r["s"]) - np.linalg.norm(vel)) <= 1e-12 * np.linalg.norm(vel)
+        assert abs(r["s"] @ r["w_hat"] + vel @ r["w_hat"]) <= 1e-12 * np.linalg.norm(vel)
+
+
+def test_ball_boltzmann_mean_closed_form():
+    """exp(-c.x / T) on the unit n-ball: along the unit vector c/|c| the
+    marginal is (1 - s^2)^((n-1)/2) exp(-l s), l = |c| / T, whose mean is
+    -I_{n/2+1}(l) / I_{n/2}(l) (modified Bessel functions); the oracle's HMC
+    chains reproduce it within five standard errors (variance by quadrature)."""
+    from scipy import integrate, special
+    n, T = 3, 1.0
+    c = np.array([1.2, -0.9, 0.0])
+    lam = np.linalg.norm(c) / T
+    e = c / np.linalg.norm(c)
+    mean = -special.iv(n / 2 + 1, lam) / special.iv(n / 2, lam)
+    dens = lambda s: (1 - s * s) ** ((n - 1) / 2) * np.exp(-lam * s)
+    Z = integrate.quad(dens, -1, 1)[0]
+    m2 = integrate.quad(lambda s: s * s * dens(s), -1, 1)[0] / Z
+    var = m2 - mean ** 2
+    A = W.ball(n, 1.0)
+    chains, steps = 400, 10
+    ends = []
+    for ch in range(chains):
+        x = np.zeros(n)
+        for k in range(steps):
+            x, st, _ = hmc.hmc_step(A, x, c, T, tau=2.0, rho=100, kappa=1e-6, seed=31, chain=ch,
+                                    step=k)
+            assert st == 0
+        ends.append(x @ e)
+    ends = np.array(ends)
+    se = np.sqrt(var / chains)
+    assert abs(ends.mean() - mean) <= 5 * se, (ends.mean(), mean, se)
