@@ -742,9 +742,82 @@ def run_hmc(args):
         print(json.dumps(line), flush=True)
 
 
+def run_reference_sized(args):
+    """The reference arm (the oracle on the host cores) of the uneven batch and
+    of the HMC workload: the same bodies, chains, Philox draws and steps as
+    the GPU line, on a bounded sample of the chains."""
+    import oracle
+    oracle.build()
+    t_all = time.perf_counter()
+    if args.workload == "batch":
+        pairs, bodies, chains = batch_workload()
+        chain0 = np.concatenate([[0], np.cumsum(chains)[:-1]]).astype(int)
+        pick = list(range(0, len(bodies), 4))  # 16 of the 64 bodies, 2 chains each
+        tau, steps, segs, dt = 6.0, max(1, args.steps), 0, 0.0
+        for i in pick:
+            X = np.zeros((2, pairs[i][0]))
+            X, _ = oracle.walk("billiard", bodies[i], X, args.warmup, tau=tau, rho=100,
+                               kappa=KAPPA, seed=SEED_WALK, step0=0, chain0=int(chain0[i]))
+            t0 = time.perf_counter()
+            _, st = oracle.walk("billiard", bodies[i], X, steps, tau=tau, rho=100, kappa=KAPPA,
+                                seed=SEED_WALK, step0=args.warmup, chain0=int(chain0[i]))
+            dt += time.perf_counter() - t0
+            segs += st["segments"]
+            if time.perf_counter() - t_all > 150.0:
+                pick = pick[:pick.index(i) + 1]
+                break
+        value = 2 * len(pick) * steps / dt
+        metric = "uneven batch billiard chain-steps/s (64 spectrahedra, one launch)"
+        sample = ("2 chains of each of %d of the 64 bodies (every 4th), steps %d-%d, %.1f s"
+                  % (len(pick), args.warmup, args.warmup + steps - 1, dt))
+        cores = oracle.num_threads()
+    else:
+        from oracle import hmc as ohmc
+        A, c, T = hmc_workload()
+        n = A.shape[0] - 1
+        # the GPU line's tau: the longest chord through the origin over the
+        # same 256 directions, here from the oracle's own intersection
+        from paper_2010_03817_gb300 import workloads as W
+        D = W.random_directions(n, 256, seed=W.BASE_SEED + 402)
+        r = oracle.intersect_batch(A, np.zeros_like(D), D)
+        tau = float(np.max(r["t_plus"] - r["t_minus"]))
+        k, segs, dt = 0, 0, 0.0
+        while k < 2 or dt < 20.0:
+            x = np.zeros(n)
+            for j in range(args.warmup):
+                x, _, _ = ohmc.hmc_step(A, x, c, T, tau=tau, rho=100, kappa=KAPPA,
+                                        seed=SEED_WALK, chain=k, step=j)
+            t0 = time.perf_counter()
+            x, _, refl = ohmc.hmc_step(A, x, c, T, tau=tau, rho=100, kappa=KAPPA,
+                                       seed=SEED_WALK, chain=k, step=args.warmup)
+            dt += time.perf_counter() - t0
+            segs += refl + 1
+            k += 1
+        value = k / dt
+        metric = "HMC-r Boltzmann chain-steps/s (S-60-60)"
+        sample = ("chains 0-%d, step %d (the GPU line's first timed step), oracle/hmc.py "
+                  "(numpy), %.1f s" % (k - 1, args.warmup, dt))
+        cores = 1
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": "chain-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload + " (oracle sample)"},
+            "oracle_calls_per_s": segs / dt,
+            "cpu_baseline": {"value": value, "unit": "chain-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample, "segments_per_s": segs / dt},
+            "e2e": {"value": value, "unit": "chain-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global WALK
     args = parse()
+    if args.impl == "reference" and args.workload in ("batch", "hmc"):
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_reference_sized(args)
+        return
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "hmc":
