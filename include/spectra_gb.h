@@ -487,7 +487,8 @@ int sp_set_solver(sp_spec* s, int kmax, double tol, double sigma_frac);
  * Parameters of the mixed-precision path: tol32 (relative residual of the
  * FP32 Lanczos of stage 1, default 1e-4), tol64 (relative residual of the
  * stage-2 power iteration, default 1e-10: t then takes a pencil Rayleigh
- * correction, whose error is quadratic in u's), delta1 (stage 2 factors at
+ * correction on the exact F and V, summed with error-free transformations,
+ * whose error is quadratic in u's), delta1 (stage 2 factors at
  * sigma0 + (t~ - sigma0)(1 - delta1), default 2e-4) and power_iters (its
  * iteration limit before the FP64 fallback, default 8).  SP_EINVAL outside
  * tol32, tol64 in (0, 1), delta1 in (0, 0.5), power_iters in [1, 64].
