@@ -727,6 +727,17 @@ __device__ __noinline__ MixResult segment_mixed(const DevSpec& sp, const MixWork
     for (int i = tid; i < m; i += SPG_THREADS) sm.u[i] = (double)sm.y32[i];
     __syncthreads();
   }
+  if (!fp64_fallback) {
+    // the stage-1 estimate sharpened before stage 2 places its shift: the
+    // pencil Rayleigh quotient of the stage-1 vector on the exact F and V is,
+    // like the Ritz estimate, never below t+ (F + t+ V is semidefinite), but
+    // its error is quadratic in the vector's instead of linear: on short
+    // chords at grazing incidence, where FP32's backward error makes the
+    // Ritz estimate overshoot by 10^-3 - 10^-2 relative and the double-float
+    // factorisation at sigma1 fail, the quotient is within about 10^-4
+    const double rq = pencil_rq(Fg, Vg, sm.u, m, sm, V32);
+    if (isfinite(rq) && rq > sigma0 && rq < t1) t1 = rq;
+  }
   double tp;
   res.status = refine_end(sp, mw, sm, Fg, Vg, Q64, sigma0, t1, fp64_fallback, &tp, &res, true);
   res.t_plus = tp;
